@@ -1,0 +1,214 @@
+"""Seeded synthetic rating matrices and initial factors.
+
+This module only draws inputs; it holds none of the ALS arithmetic. Both the
+CUDA path and the FP64 oracle take what it returns, so the two always start
+from identical data.
+
+Workloads (shapes follow the rating matrices of Sec. 5 and Sec. 6.1, where R
+is n_u x n_m with missing entries and integer 1-5 ratings for the
+recommender data):
+
+* ``uniform_lowrank``: R = U V^T + N(0, sigma^2) on a uniformly drawn
+  fraction of the cells (the small 1000 x 500, n_f = 10 case).
+* ``zipf_ratings``: cells drawn from a product of two Zipf(s) popularity laws
+  over randomly permuted user and item ranks, deduplicated until exactly
+  ``nnz`` distinct cells exist; ratings are clip(rint(3 + u.v + eps), 1, 5)
+  with a rank-n_f truth (the 100k x 20k, 10M-entry, n_f = 32 case and its
+  larger relatives).
+
+Factor entries of the truth are N(0, 1/sqrt(n_f)) read as a *variance*, so
+u.v has unit variance. Observed cells are split 90/10 into train/test.
+
+The initial factor M^(0) ("initialize M randomly", Sec. 2.1 Step 1 and
+Algorithm 2) is drawn from a counter-based generator: SplitMix64 (Steele,
+Lea and Flood, OOPSLA 2014) feeding the Box-Muller transform, so any element
+can be recomputed from (seed, index) alone.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(counter: np.ndarray, seed: int) -> np.ndarray:
+    """SplitMix64 output for each counter value (uint64 array in, uint64 out).
+
+    State for counter c is seed + (c + 1) * golden; the output is the standard
+    SplitMix64 finaliser of that state.
+    """
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) + (counter.astype(np.uint64) + np.uint64(1)) * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        return z ^ (z >> np.uint64(31))
+
+
+def _uniform_open(counter: np.ndarray, seed: int) -> np.ndarray:
+    """Uniform doubles in (0, 1]: top 53 bits of SplitMix64, shifted by one ulp."""
+    z = splitmix64(counter, seed) >> np.uint64(11)
+    return (z.astype(np.float64) + 1.0) * (1.0 / 9007199254740992.0)
+
+
+def init_factor(n: int, f: int, seed: int) -> np.ndarray:
+    """Initial factor (n x f, float32) with i.i.d. N(0, 1/sqrt(f)) entries.
+
+    Element e (row-major) uses counters 2e and 2e+1 for the Box-Muller pair and
+    keeps the cosine branch.
+    """
+    e = np.arange(n * f, dtype=np.uint64)
+    u1 = _uniform_open(2 * e, seed)
+    u2 = _uniform_open(2 * e + np.uint64(1), seed)
+    z = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+    std = (1.0 / np.sqrt(f)) ** 0.5
+    return (z * std).astype(np.float32).reshape(n, f)
+
+
+@dataclass
+class CSR:
+    """Compressed rows: int64 indptr, int32 sorted unique indices, float32 values."""
+    n_rows: int
+    n_cols: int
+    indptr: np.ndarray
+    indices: np.ndarray
+    values: np.ndarray
+
+    @property
+    def nnz(self) -> int:
+        return int(self.indices.shape[0])
+
+    def row_lengths(self) -> np.ndarray:
+        return np.diff(self.indptr)
+
+
+@dataclass
+class RatingProblem:
+    n_u: int
+    n_m: int
+    f: int
+    train_rows: CSR      # users x items (CSR of train)
+    train_cols: CSR      # items x users (CSR of the transpose = CSC of train)
+    test_u: np.ndarray   # int32 test user ids
+    test_m: np.ndarray   # int32 test item ids
+    test_r: np.ndarray   # float32 test ratings
+    U_true: np.ndarray
+    M_true: np.ndarray
+
+
+def coo_to_csr(rows: np.ndarray, cols: np.ndarray, vals: np.ndarray,
+               n_rows: int, n_cols: int) -> CSR:
+    """Build a CSR with indices sorted ascending inside each row."""
+    key = rows.astype(np.int64) * np.int64(n_cols) + cols.astype(np.int64)
+    order = np.argsort(key, kind="stable")
+    r = rows[order]
+    counts = np.bincount(r, minlength=n_rows).astype(np.int64)
+    indptr = np.zeros(n_rows + 1, dtype=np.int64)
+    np.cumsum(counts, out=indptr[1:])
+    return CSR(n_rows, n_cols, indptr,
+               np.ascontiguousarray(cols[order].astype(np.int32)),
+               np.ascontiguousarray(vals[order].astype(np.float32)))
+
+
+def _truth(n_u: int, n_m: int, f: int, rng: np.random.Generator):
+    std = (1.0 / np.sqrt(f)) ** 0.5
+    U = rng.standard_normal((n_u, f)) * std
+    M = rng.standard_normal((n_m, f)) * std
+    return U, M
+
+
+def _dots(U: np.ndarray, M: np.ndarray, ii: np.ndarray, jj: np.ndarray) -> np.ndarray:
+    out = np.empty(ii.shape[0], dtype=np.float64)
+    step = 1 << 21
+    for s in range(0, ii.shape[0], step):
+        out[s:s + step] = np.einsum("ij,ij->i", U[ii[s:s + step]], M[jj[s:s + step]])
+    return out
+
+
+def _split(ii, jj, rr, n_u, n_m, f, U, M, rng, test_frac=0.1) -> RatingProblem:
+    n = ii.shape[0]
+    perm = rng.permutation(n)
+    n_test = int(round(n * test_frac))
+    te, tr = perm[:n_test], perm[n_test:]
+    rows = coo_to_csr(ii[tr], jj[tr], rr[tr], n_u, n_m)
+    cols = coo_to_csr(jj[tr], ii[tr], rr[tr], n_m, n_u)
+    return RatingProblem(n_u, n_m, f, rows, cols,
+                         ii[te].astype(np.int32), jj[te].astype(np.int32),
+                         rr[te].astype(np.float32), U, M)
+
+
+def uniform_lowrank(n_u: int, n_m: int, f: int, density: float, noise_sd: float,
+                    seed: int) -> RatingProblem:
+    """R = U V^T + N(0, noise_sd^2) observed on round(density * n_u * n_m) uniform cells."""
+    rng = np.random.default_rng(seed)
+    U, M = _truth(n_u, n_m, f, rng)
+    nnz = int(round(density * n_u * n_m))
+    cells = rng.choice(n_u * n_m, size=nnz, replace=False)
+    ii = (cells // n_m).astype(np.int64)
+    jj = (cells % n_m).astype(np.int64)
+    rr = _dots(U, M, ii, jj) + rng.standard_normal(nnz) * noise_sd
+    return _split(ii, jj, rr.astype(np.float32), n_u, n_m, f, U, M, rng)
+
+
+def _sorted_unique(a: np.ndarray) -> np.ndarray:
+    a = np.sort(a)
+    if a.shape[0] == 0:
+        return a
+    keep = np.empty(a.shape[0], dtype=bool)
+    keep[0] = True
+    np.not_equal(a[1:], a[:-1], out=keep[1:])
+    return a[keep]
+
+
+def zipf_cells(n_u: int, n_m: int, nnz: int, s_u: float, s_m: float,
+               rng: np.random.Generator):
+    """Exactly ``nnz`` distinct (user, item) cells from a product of Zipf laws."""
+    if nnz > n_u * n_m:
+        raise ValueError("more cells requested than the matrix holds")
+    pu = 1.0 / np.arange(1, n_u + 1, dtype=np.float64) ** s_u
+    pm = 1.0 / np.arange(1, n_m + 1, dtype=np.float64) ** s_m
+    pu = pu[rng.permutation(n_u)]
+    pm = pm[rng.permutation(n_m)]
+    cu = np.cumsum(pu / pu.sum())
+    cm = np.cumsum(pm / pm.sum())
+    have = np.empty(0, dtype=np.int64)
+    while have.shape[0] < nnz:
+        want = int((nnz - have.shape[0]) * 2.0) + 1024
+        i = np.minimum(np.searchsorted(cu, rng.random(want)), n_u - 1)
+        j = np.minimum(np.searchsorted(cm, rng.random(want)), n_m - 1)
+        have = _sorted_unique(np.concatenate([have, i.astype(np.int64) * n_m + j]))
+    keep = rng.choice(have.shape[0], size=nnz, replace=False)
+    cells = have[np.sort(keep)]
+    return cells // n_m, cells % n_m
+
+
+def zipf_ratings(n_u: int, n_m: int, f: int, nnz: int, zipf_s: float,
+                 noise_sd: float, seed: int) -> RatingProblem:
+    """Integer 1-5 ratings clip(rint(3 + u.v + eps), 1, 5) on Zipf-popular cells."""
+    rng = np.random.default_rng(seed)
+    U, M = _truth(n_u, n_m, f, rng)
+    ii, jj = zipf_cells(n_u, n_m, nnz, zipf_s, zipf_s, rng)
+    rr = 3.0 + _dots(U, M, ii, jj) + rng.standard_normal(ii.shape[0]) * noise_sd
+    rr = np.clip(np.rint(rr), 1.0, 5.0)
+    return _split(ii, jj, rr.astype(np.float32), n_u, n_m, f, U, M, rng)
+
+
+# Named workloads. "small" is the case the oracle finishes in seconds;
+# "zipf_100k" is the 100k x 20k, 10M-entry, n_f = 32 rating matrix.
+WORKLOADS = {
+    "small": dict(kind="uniform", n_u=1000, n_m=500, f=10, density=0.05,
+                  noise_sd=0.1, lam=0.1, budget=0.5, sweeps=10),
+    "zipf_100k": dict(kind="zipf", n_u=100_000, n_m=20_000, f=32, nnz=10_000_000,
+                      zipf_s=1.0, noise_sd=0.5, lam=0.05, budget=0.25, sweeps=15),
+}
+
+
+def make_workload(name: str, seed: int = 1, **over) -> RatingProblem:
+    w = dict(WORKLOADS[name])
+    w.update(over)
+    if w["kind"] == "uniform":
+        return uniform_lowrank(w["n_u"], w["n_m"], w["f"], w["density"], w["noise_sd"], seed)
+    return zipf_ratings(w["n_u"], w["n_m"], w["f"], w["nnz"], w["zipf_s"], w["noise_sd"], seed)

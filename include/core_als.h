@@ -1,0 +1,202 @@
+/*
+ * core_als.h - C ABI of the GB300 (sm_103a) core-elements ALS library.
+ *
+ * The method (Xue, Li, Zhang, Meng, "Core-elements Subsampling for
+ * Alternating Least Squares", arXiv 2509.18024):
+ *
+ *   A rating matrix R (n_u x n_m) with missing entries is factorised as
+ *   R ~ U M^T with rank n_f (Sec. 2.1). Each sweep of Algorithm 2 updates
+ *   every user row, then every item row. For a row i with observed index set
+ *   I_i (|I_i| = n_i), the design slice X = Y[I_i] (n_i x n_f) is made of the
+ *   other side's factor rows in ascending index order, and
+ *
+ *     CES (Algorithm 1):  in every column a of X keep the s_i = floor(n_i r)
+ *                         entries of largest |x_ka| and zero the rest: X*.
+ *     Eq. (core_ui/mj):   x_i = (X*^T X + lambda n_i E)^{-1} X*^T r_i.
+ *
+ *   With budget r = 1 (or gram_mode ALS_GRAM_FULL) this is the full ALS
+ *   update of Eq. (U format) / (M format).
+ *
+ * Conventions for every call:
+ *   - Pointers are DEVICE pointers unless the parameter name ends in _host.
+ *   - Matrices are row-major, FP32 unless stated; factor rows have n_f
+ *     contiguous floats (row stride n_f).
+ *   - A side of the rating matrix is passed as compressed rows (als_csr):
+ *     the user side is R in CSR, the item side is R^T in CSR (= R in CSC).
+ *     Indices inside a row must be sorted ascending and unique; values finite.
+ *   - All work is enqueued on the handle's CUDA stream. Calls return when the
+ *     work is enqueued, except where a _host output is filled (those
+ *     synchronise the stream) and the first call on a new rating structure
+ *     (see als_prepare).
+ *   - The caller owns every buffer passed in; the library never frees caller
+ *     memory. The handle owns its workspace (als_workspace_bytes).
+ *   - Return value: ALS_OK (0) or a negative ALS_ERR_* code. Nothing is
+ *     written to outputs after an argument error. als_status_string() names
+ *     a code; als_last_error() gives the handle's last message.
+ */
+#ifndef CORE_ALS_H
+#define CORE_ALS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ALS_OK 0
+#define ALS_ERR_ARG (-1)            /* bad argument (null pointer, size, option) */
+#define ALS_ERR_CSR (-2)            /* unsorted, duplicate or out-of-range index, bad indptr */
+#define ALS_ERR_NONFINITE (-3)      /* NaN/Inf rating value */
+#define ALS_ERR_CUDA (-4)           /* a CUDA runtime call failed */
+#define ALS_ERR_TIMEOUT (-5)        /* a bounded device wait ran out */
+#define ALS_ERR_OOM (-6)            /* device allocation failed or workspace cap hit */
+#define ALS_ERR_DEVICE_BOUNDS (-7)  /* a device-side bounds check fired */
+#define ALS_ERR_UNSUPPORTED (-8)    /* option combination not built (e.g. n_f > 32 on FP32) */
+
+/* Regulariser: weighted lambda n_i (Eq. object function) or plain lambda. */
+#define ALS_REG_WEIGHTED 0
+#define ALS_REG_PLAIN 1
+
+/* System matrix: X*^T X (Eq. core_ui, the paper's form, solved by LU with
+ * partial pivoting), X*^T X* (symmetric variant, Cholesky), or X^T X (full
+ * ALS, Eq. U format, Cholesky). */
+#define ALS_GRAM_ASYM 0
+#define ALS_GRAM_SYM 1
+#define ALS_GRAM_FULL 2
+
+/* Arithmetic of the Gram assembly. */
+#define ALS_FP32 0
+#define ALS_TF32 1
+#define ALS_BF16 2
+
+/* Per-row flags written by the solve. */
+#define ALS_FLAG_RATIO 1     /* pivot ratio above pivot_ratio_max */
+#define ALS_FLAG_SINGULAR 2  /* zero / non-positive pivot: the row was set to 0 */
+
+typedef struct als_csr {
+    int64_t n_rows;          /* rows of this side (users, or items for R^T) */
+    int64_t n_cols;          /* rows of the other side's factor */
+    int64_t nnz;
+    const int64_t* indptr;   /* device, n_rows + 1, indptr[0] = 0, indptr[n_rows] = nnz */
+    const int32_t* indices;  /* device, nnz, in [0, n_cols), ascending within a row */
+    const float* values;     /* device, nnz, finite ratings */
+} als_csr;
+
+typedef struct als_options {
+    int n_f;                 /* rank; 1..32 in this build */
+    float lambda;            /* regularisation */
+    double budget;           /* CES rate r in [0, 1]; s_i = floor(n_i * r) per column */
+    int64_t min_keep;        /* 0 = off; else s_i = min(n_i, max(s_i, min_keep)) */
+    int reg_mode;            /* ALS_REG_* */
+    int gram_mode;           /* ALS_GRAM_* */
+    int precision;           /* ALS_FP32 (others: ALS_ERR_UNSUPPORTED in this build) */
+    double pivot_ratio_max;  /* flag threshold on max pivot / min pivot, e.g. 1e6 */
+} als_options;
+
+typedef struct als_report {
+    int64_t rows_flagged;     /* rows with ALS_FLAG_RATIO set, last half-sweep */
+    int64_t rows_singular;    /* rows with ALS_FLAG_SINGULAR set, last half-sweep */
+    double max_pivot_ratio;   /* largest pivot ratio seen, last half-sweep */
+    double test_rmse;         /* als_fit: test RMSE after the last sweep (NaN if no test set) */
+    double objective;         /* als_fit: Eq. (object function) after the last sweep */
+    int sweeps_done;
+} als_report;
+
+typedef struct als_handle als_handle;
+
+/* Default options: n_f = 32, lambda = 0.05, budget = 0.25, weighted lambda,
+ * asymmetric Gram, FP32, pivot_ratio_max = 1e6. */
+void als_default_options(als_options* opt_host);
+
+/* Create a handle bound to the current CUDA device and to cuda_stream
+ * (a cudaStream_t; NULL = the legacy default stream). */
+int als_create(als_handle** handle_host, const als_options* opt_host, void* cuda_stream);
+int als_destroy(als_handle* h);
+int als_set_stream(als_handle* h, void* cuda_stream);
+int als_get_options(const als_handle* h, als_options* opt_host);
+
+/* Validate one side's rating structure (sorted unique in-range indices,
+ * monotone indptr, finite values) and build its row plan (rows bucketed by
+ * length). Synchronises the stream. Later calls with the same indptr
+ * pointer, n_rows and nnz reuse the plan; other calls prepare implicitly.
+ * Call it once per structure before capturing work into a CUDA graph. */
+int als_prepare(als_handle* h, const als_csr* R_side);
+
+/* One half-sweep of Algorithm 2 for the side R_side: for every row i,
+ * CES on Y[I_i] and Eq. (core_ui) (or Eq. U format for ALS_GRAM_FULL).
+ * Y_in: n_cols x n_f; X_out: n_rows x n_f (rows with n_i = 0 get 0).
+ * flags_out (nullable): int32 per row, ALS_FLAG_* bits. Y_in and X_out
+ * must not overlap. */
+int als_half_sweep(als_handle* h, const als_csr* R_side, const float* Y_in, float* X_out,
+                   int32_t* flags_out);
+
+/* CES masks only (Algorithm 1 applied to every row's slice): masks_out holds
+ * nnz x ceil(n_f/32) uint32 words in CSR storage order; bit (a mod 32) of
+ * word a/32 is set when element (k, a) is kept. */
+int als_select(als_handle* h, const als_csr* R_side, const float* Y_in, uint32_t* masks_out);
+
+/* The assembled systems of Eq. (core_ui): G_out n_rows x n_f x n_f (row-major,
+ * regulariser already on the diagonal), b_out n_rows x n_f. */
+int als_assemble(als_handle* h, const als_csr* R_side, const float* Y_in, float* G_out, float* b_out);
+
+/* Solve n_rows independent systems G x = b (G n_rows x n_f x n_f, b n_rows x
+ * n_f) with the handle's method (LU with partial pivoting for ALS_GRAM_ASYM,
+ * Cholesky otherwise). flags_out nullable. */
+int als_solve(als_handle* h, int64_t n_rows, const float* G, const float* b, float* X_out,
+              int32_t* flags_out);
+
+/* Sum of squared errors over n entries (r_e - u_{iu_e} . m_{im_e})^2,
+ * accumulated in FP64 in a fixed order; written to sse_host (synchronises). */
+int als_eval_sse(als_handle* h, int64_t n, const int32_t* iu, const int32_t* im, const float* r,
+                 const float* U, const float* M, double* sse_host);
+
+/* As als_eval_sse, but the FP64 sum is written to sse_dev (one double in
+ * device memory) without synchronising. */
+int als_eval_sse_async(als_handle* h, int64_t n, const int32_t* iu, const int32_t* im, const float* r,
+                       const float* U, const float* M, double* sse_dev);
+
+/* Kernel timing: while enabled, every kernel the handle launches is
+ * bracketed by CUDA events on the handle's stream. als_kernel_time
+ * synchronises and returns the summed event time (ms) and the number of
+ * launches of the kernels whose family name is `name` ("cta_rows",
+ * "warp_rows", "solve_rows", "sse", ...) since profiling was enabled;
+ * name NULL sums every family. Enabling again resets the sums. */
+int als_profile(als_handle* h, int enable);
+int als_kernel_time(als_handle* h, const char* name, double* ms_host, int64_t* launches_host);
+
+/* Counters of the last half-sweep (synchronises). */
+int als_get_report(als_handle* h, als_report* rep_host);
+
+/* One full sweep: users from M (into U), then items from the new U (into M). */
+int als_sweep(als_handle* h, const als_csr* R_users, const als_csr* R_items, float* U, float* M);
+
+/* Algorithm 2: `sweeps` sweeps starting from M (in: M^(0), out: result);
+ * U is output only. If test entries are given (n_test > 0) the report gets
+ * the test RMSE after the last sweep. rep_host nullable. */
+int als_fit(als_handle* h, const als_csr* R_users, const als_csr* R_items, int sweeps,
+            float* U, float* M, int64_t n_test, const int32_t* test_u, const int32_t* test_m,
+            const float* test_r, als_report* rep_host);
+
+/* als_fit from HOST buffers: copies both sides' CSR arrays, M^(0) and the
+ * test entries to the device, fits, and copies U and M back to the host.
+ * Uses the handle's workspace for device copies. */
+int als_fit_host(als_handle* h, int64_t n_u, int64_t n_m, int64_t nnz,
+                 const int64_t* user_indptr_host, const int32_t* user_indices_host,
+                 const float* user_values_host, const int64_t* item_indptr_host,
+                 const int32_t* item_indices_host, const float* item_values_host, int sweeps,
+                 float* U_host, float* M_host, int64_t n_test, const int32_t* test_u_host,
+                 const int32_t* test_m_host, const float* test_r_host, als_report* rep_host);
+
+/* Bytes of device workspace the handle currently holds. */
+int64_t als_workspace_bytes(const als_handle* h);
+
+/* Number of kernel launches the handle has enqueued since creation. */
+int64_t als_launch_count(const als_handle* h);
+
+const char* als_status_string(int status);
+const char* als_last_error(const als_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CORE_ALS_H */

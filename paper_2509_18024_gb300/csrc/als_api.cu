@@ -1,0 +1,654 @@
+// Host side of the C ABI declared in include/core_als.h: handle, workspace,
+// structure validation, row planning and kernel launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "core_als.h"
+#include "als_kernels.cuh"
+
+namespace {
+
+using als::Counters;
+using als::Params;
+using als::Side;
+
+// Row plan of one side: rows bucketed by length (warp rows n_i <= 32, CTA
+// rows longer, sorted by length descending so the longest start first).
+struct Plan {
+    const int64_t* indptr = nullptr;
+    int64_t n_rows = 0, nnz = 0, n_cols = 0;
+    int n_warp = 0, n_cta = 0;
+    int64_t max_len = 0;
+    int32_t* d_lists = nullptr;  // [warp rows | cta rows]
+};
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct als_handle {
+    als_options opt;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::vector<Plan> plans;
+    DevBuf g_aug;     // augmented systems of CTA rows
+    DevBuf misc;      // counters + eval partials + error word
+    DevBuf host_in;   // device copies for als_fit_host
+    int64_t launches = 0;
+    std::string last_error;
+    // Kernel timing (als_profile): events bracketing each launch.
+    bool profiling = false;
+    struct Timed {
+        const char* family;
+        cudaEvent_t start, stop;
+    };
+    std::vector<Timed> timed;
+    std::vector<cudaEvent_t> event_pool;
+    const char* pending_family = nullptr;
+    cudaEvent_t pending_start = nullptr;
+};
+
+namespace {
+
+int set_err(als_handle* h, int code, const char* fmt, ...) {
+    if (h) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        h->last_error = buf;
+    }
+    return code;
+}
+
+#define ALS_CUDA(h, call)                                                                       \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return set_err((h), ALS_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));   \
+    } while (0)
+
+cudaEvent_t take_event(als_handle* h) {
+    if (!h->event_pool.empty()) {
+        cudaEvent_t e = h->event_pool.back();
+        h->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+// Marks the start of a launch of kernel family `family` (timed when
+// profiling is on).
+void pre_launch(als_handle* h, const char* family) {
+    if (!h->profiling) return;
+    h->pending_family = family;
+    h->pending_start = take_event(h);
+    if (h->pending_start) cudaEventRecord(h->pending_start, h->stream);
+}
+
+void post_launch(als_handle* h) {
+    if (!h->profiling || !h->pending_start) return;
+    cudaEvent_t stop = take_event(h);
+    if (!stop) return;
+    cudaEventRecord(stop, h->stream);
+    h->timed.push_back({h->pending_family, h->pending_start, stop});
+    h->pending_start = nullptr;
+}
+
+#define ALS_LAUNCH(h, family, ...)                                                               \
+    do {                                                                                        \
+        pre_launch((h), (family));                                                              \
+        __VA_ARGS__;                                                                            \
+        post_launch(h);                                                                         \
+        (h)->launches++;                                                                        \
+        cudaError_t e_ = cudaGetLastError();                                                    \
+        if (e_ != cudaSuccess)                                                                  \
+            return set_err((h), ALS_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e_)); \
+    } while (0)
+
+int ensure(als_handle* h, DevBuf& b, size_t bytes) {
+    if (b.bytes >= bytes) return ALS_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    size_t want = std::max(bytes, (size_t)256);
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(h, ALS_ERR_OOM, "cudaMalloc(%zu) failed: %s", want, cudaGetErrorString(e));
+    }
+    b.bytes = want;
+    return ALS_OK;
+}
+
+int padded_width(int f) {
+    if (f <= 8) return 8;
+    if (f <= 16) return 16;
+    if (f <= 32) return 32;
+    return 0;
+}
+
+Params make_params(const als_options& o) {
+    Params p;
+    p.f = o.n_f;
+    p.lambda = o.lambda;
+    p.budget = o.budget;
+    p.min_keep = o.min_keep;
+    p.reg_mode = o.reg_mode;
+    p.gram_mode = o.gram_mode;
+    p.ratio_max = (float)o.pivot_ratio_max;
+    return p;
+}
+
+int check_options(als_handle* h, const als_options* o) {
+    if (!o) return set_err(h, ALS_ERR_ARG, "options are null");
+    if (o->n_f < 1) return set_err(h, ALS_ERR_ARG, "n_f must be >= 1");
+    if (o->n_f > 32) return set_err(h, ALS_ERR_UNSUPPORTED, "n_f > 32 is not built in this library");
+    if (!(o->budget >= 0.0 && o->budget <= 1.0)) return set_err(h, ALS_ERR_ARG, "budget must be in [0, 1]");
+    if (!(o->lambda >= 0.0f) || !std::isfinite(o->lambda)) return set_err(h, ALS_ERR_ARG, "lambda must be >= 0");
+    if (o->reg_mode != ALS_REG_WEIGHTED && o->reg_mode != ALS_REG_PLAIN) return set_err(h, ALS_ERR_ARG, "bad reg_mode");
+    if (o->gram_mode < ALS_GRAM_ASYM || o->gram_mode > ALS_GRAM_FULL) return set_err(h, ALS_ERR_ARG, "bad gram_mode");
+    if (o->precision != ALS_FP32) return set_err(h, ALS_ERR_UNSUPPORTED, "only ALS_FP32 is built in this library");
+    if (o->min_keep < 0) return set_err(h, ALS_ERR_ARG, "min_keep must be >= 0");
+    if (!(o->pivot_ratio_max > 0.0)) return set_err(h, ALS_ERR_ARG, "pivot_ratio_max must be > 0");
+    return ALS_OK;
+}
+
+int check_csr(als_handle* h, const als_csr* R) {
+    if (!R) return set_err(h, ALS_ERR_ARG, "rating structure is null");
+    if (R->n_rows < 0 || R->n_cols < 0 || R->nnz < 0) return set_err(h, ALS_ERR_ARG, "negative size");
+    if (R->n_rows > 0x7fffffff || R->n_cols > 0x7fffffff) return set_err(h, ALS_ERR_ARG, "more than 2^31-1 rows");
+    if (!R->indptr) return set_err(h, ALS_ERR_ARG, "indptr is null");
+    if (R->nnz > 0 && (!R->indices || !R->values)) return set_err(h, ALS_ERR_ARG, "indices/values are null");
+    return ALS_OK;
+}
+
+Counters* counters(als_handle* h) { return reinterpret_cast<Counters*>(h->misc.p); }
+double* eval_partials(als_handle* h) {
+    return reinterpret_cast<double*>(reinterpret_cast<char*>(h->misc.p) + 256);
+}
+double* eval_out(als_handle* h) { return eval_partials(h) + als::kEvalBlocks; }
+unsigned* valid_err(als_handle* h) { return reinterpret_cast<unsigned*>(eval_out(h) + 1); }
+constexpr size_t kMiscBytes = 256 + (als::kEvalBlocks + 1) * sizeof(double) + 64;
+
+int build_plan(als_handle* h, const als_csr* R, Plan** out) {
+    for (auto& p : h->plans) {
+        if (p.indptr == R->indptr && p.n_rows == R->n_rows && p.nnz == R->nnz && p.n_cols == R->n_cols) {
+            *out = &p;
+            return ALS_OK;
+        }
+    }
+    // Validate the structure on the device, then plan on the host.
+    cudaStream_t st = h->stream;
+    ALS_CUDA(h, cudaMemsetAsync(valid_err(h), 0, sizeof(unsigned), st));
+    if (R->n_rows > 0) {
+        int blocks = (int)std::min<int64_t>((R->n_rows + 255) / 256, 4096);
+        ALS_LAUNCH(h, "validate", als::k_validate<<<blocks, 256, 0, st>>>(R->indptr, R->indices, R->values, R->n_rows, R->n_cols, R->nnz,
+                                                valid_err(h)));
+    }
+    std::vector<int64_t> indptr(R->n_rows + 1);
+    unsigned err = 0;
+    ALS_CUDA(h, cudaMemcpyAsync(indptr.data(), R->indptr, sizeof(int64_t) * (R->n_rows + 1), cudaMemcpyDeviceToHost, st));
+    ALS_CUDA(h, cudaMemcpyAsync(&err, valid_err(h), sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    ALS_CUDA(h, cudaStreamSynchronize(st));
+    if (indptr[0] != 0 || indptr[R->n_rows] != R->nnz) err |= 1u;
+    if (err & 1u) return set_err(h, ALS_ERR_CSR, "indptr is not monotone from 0 to nnz");
+    if (err & 2u) return set_err(h, ALS_ERR_CSR, "indices out of range, unsorted or duplicated inside a row");
+    if (err & 4u) return set_err(h, ALS_ERR_NONFINITE, "non-finite rating value");
+
+    std::vector<int32_t> warp_rows, cta_rows;
+    int64_t max_len = 0;
+    for (int64_t i = 0; i < R->n_rows; ++i) {
+        int64_t len = indptr[i + 1] - indptr[i];
+        max_len = std::max(max_len, len);
+        if (len <= als::kWarpRowMax) warp_rows.push_back((int32_t)i);
+        else cta_rows.push_back((int32_t)i);
+    }
+    std::stable_sort(cta_rows.begin(), cta_rows.end(), [&](int32_t a, int32_t b) {
+        return indptr[a + 1] - indptr[a] > indptr[b + 1] - indptr[b];
+    });
+    Plan p;
+    p.indptr = R->indptr;
+    p.n_rows = R->n_rows;
+    p.nnz = R->nnz;
+    p.n_cols = R->n_cols;
+    p.n_warp = (int)warp_rows.size();
+    p.n_cta = (int)cta_rows.size();
+    p.max_len = max_len;
+    std::vector<int32_t> lists(warp_rows);
+    lists.insert(lists.end(), cta_rows.begin(), cta_rows.end());
+    size_t bytes = std::max<size_t>(lists.size(), 1) * sizeof(int32_t);
+    cudaError_t e = cudaMalloc(&p.d_lists, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(h, ALS_ERR_OOM, "cudaMalloc(plan) failed");
+    }
+    if (!lists.empty()) {
+        ALS_CUDA(h, cudaMemcpyAsync(p.d_lists, lists.data(), lists.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        ALS_CUDA(h, cudaStreamSynchronize(st));
+    }
+    // Keep a small bounded cache of plans.
+    if (h->plans.size() >= 8) {
+        cudaFree(h->plans.front().d_lists);
+        h->plans.erase(h->plans.begin());
+    }
+    h->plans.push_back(p);
+    *out = &h->plans.back();
+    return ALS_OK;
+}
+
+template <int F>
+size_t cta_smem_bytes() {
+    return sizeof(als::CtaRowSmem<F>);
+}
+
+template <int F>
+int configure_kernels(als_handle* h) {
+    // Per-function attribute of the current device; cheap to repeat.
+    ALS_CUDA(h, cudaFuncSetAttribute(als::k_cta_rows<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)cta_smem_bytes<F>()));
+    return ALS_OK;
+}
+
+// mode 0: solve into X_out; 1: assembled systems into G_out/b_out; 2: masks only.
+template <int F>
+int run_side(als_handle* h, const Plan& pl, const Side& side, int mode, float* X_out, int32_t* flags_out,
+             uint32_t* masks_out, float* G_out, float* b_out) {
+    int rc = configure_kernels<F>(h);
+    if (rc) return rc;
+    cudaStream_t st = h->stream;
+    Params p = make_params(h->opt);
+    const int32_t* warp_list = pl.d_lists;
+    const int32_t* cta_list = pl.d_lists + pl.n_warp;
+    const int n_lists_max = std::max(pl.n_warp, pl.n_cta);
+    if (mode == 1) {
+        rc = ensure(h, h->g_aug, (size_t)std::max(n_lists_max, 1) * F * (F + 1) * sizeof(float));
+    } else {
+        rc = ensure(h, h->g_aug, (size_t)std::max(pl.n_cta, 1) * F * (F + 1) * sizeof(float));
+    }
+    if (rc) return rc;
+    float* G_aug = reinterpret_cast<float*>(h->g_aug.p);
+    if (pl.n_cta > 0) {
+        ALS_LAUNCH(h, "cta_rows", als::k_cta_rows<F><<<pl.n_cta, als::kCtaThreads, cta_smem_bytes<F>(), st>>>(side, p, cta_list, pl.n_cta,
+                                                                                  mode, G_aug, masks_out));
+        if (mode == 0) {
+            ALS_LAUNCH(h, "solve_rows", als::k_solve_rows<F><<<(pl.n_cta + 7) / 8, 256, 0, st>>>(G_aug, cta_list, pl.n_cta, p, X_out, flags_out,
+                                                                     counters(h)));
+        } else if (mode == 1) {
+            ALS_LAUNCH(h, "unpack_aug", als::k_unpack_aug<F><<<1024, 256, 0, st>>>(G_aug, cta_list, pl.n_cta, p.f, G_out, b_out));
+        }
+    }
+    if (pl.n_warp > 0) {
+        ALS_LAUNCH(h, "warp_rows", als::k_warp_rows<F><<<(pl.n_warp + 7) / 8, 256, 0, st>>>(side, p, warp_list, pl.n_warp, mode, X_out,
+                                                                 flags_out, masks_out, G_aug, counters(h)));
+        if (mode == 1) {
+            ALS_LAUNCH(h, "unpack_aug", als::k_unpack_aug<F><<<1024, 256, 0, st>>>(G_aug, warp_list, pl.n_warp, p.f, G_out, b_out));
+        }
+    }
+    return ALS_OK;
+}
+
+int dispatch_side(als_handle* h, const als_csr* R, const float* Y, int mode, float* X_out, int32_t* flags_out,
+                  uint32_t* masks_out, float* G_out, float* b_out) {
+    int rc = check_csr(h, R);
+    if (rc) return rc;
+    if (!Y && R->n_cols > 0) return set_err(h, ALS_ERR_ARG, "factor Y is null");
+    Plan* pl = nullptr;
+    rc = build_plan(h, R, &pl);
+    if (rc) return rc;
+    Side side;
+    side.indptr = R->indptr;
+    side.indices = R->indices;
+    side.values = R->values;
+    side.Y = Y;
+    side.n_rows = R->n_rows;
+    side.n_cols = R->n_cols;
+    if (mode == 0) ALS_CUDA(h, cudaMemsetAsync(counters(h), 0, sizeof(Counters), h->stream));
+    switch (padded_width(h->opt.n_f)) {
+        case 8: return run_side<8>(h, *pl, side, mode, X_out, flags_out, masks_out, G_out, b_out);
+        case 16: return run_side<16>(h, *pl, side, mode, X_out, flags_out, masks_out, G_out, b_out);
+        case 32: return run_side<32>(h, *pl, side, mode, X_out, flags_out, masks_out, G_out, b_out);
+        default: return set_err(h, ALS_ERR_UNSUPPORTED, "n_f not supported");
+    }
+}
+
+template <int F>
+int solve_systems(als_handle* h, int64_t n_rows, const float* G, const float* b, float* X_out, int32_t* flags_out) {
+    cudaStream_t st = h->stream;
+    Params p = make_params(h->opt);
+    int rc = ensure(h, h->g_aug, (size_t)std::max<int64_t>(n_rows, 1) * F * (F + 1) * sizeof(float));
+    if (rc) return rc;
+    float* G_aug = reinterpret_cast<float*>(h->g_aug.p);
+    ALS_CUDA(h, cudaMemsetAsync(counters(h), 0, sizeof(Counters), st));
+    ALS_LAUNCH(h, "pack_aug", als::k_pack_aug<F><<<1024, 256, 0, st>>>(G, b, n_rows, p.f, G_aug));
+    ALS_LAUNCH(h, "solve_rows", als::k_solve_rows<F><<<(int)((n_rows + 7) / 8), 256, 0, st>>>(G_aug, nullptr, (int)n_rows, p, X_out, flags_out,
+                                                                  counters(h)));
+    return ALS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void als_default_options(als_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->n_f = 32;
+    o->lambda = 0.05f;
+    o->budget = 0.25;
+    o->min_keep = 0;
+    o->reg_mode = ALS_REG_WEIGHTED;
+    o->gram_mode = ALS_GRAM_ASYM;
+    o->precision = ALS_FP32;
+    o->pivot_ratio_max = 1e6;
+}
+
+int als_create(als_handle** out, const als_options* opt, void* stream) {
+    if (!out) return ALS_ERR_ARG;
+    *out = nullptr;
+    int rc = check_options(nullptr, opt);
+    if (rc) return rc;
+    als_handle* h = new als_handle();
+    h->opt = *opt;
+    h->stream = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return ALS_ERR_CUDA;
+    }
+    rc = ensure(h, h->misc, kMiscBytes);
+    if (rc) {
+        delete h;
+        return rc;
+    }
+    if (cudaMemset(h->misc.p, 0, kMiscBytes) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(h->misc.p);
+        delete h;
+        return ALS_ERR_CUDA;
+    }
+    *out = h;
+    return ALS_OK;
+}
+
+int als_destroy(als_handle* h) {
+    if (!h) return ALS_ERR_ARG;
+    cudaStreamSynchronize(h->stream);
+    for (auto& p : h->plans) cudaFree(p.d_lists);
+    for (auto& t : h->timed) {
+        cudaEventDestroy(t.start);
+        cudaEventDestroy(t.stop);
+    }
+    for (auto e : h->event_pool) cudaEventDestroy(e);
+    for (DevBuf* b : {&h->g_aug, &h->misc, &h->host_in})
+        if (b->p) cudaFree(b->p);
+    delete h;
+    return ALS_OK;
+}
+
+int als_set_stream(als_handle* h, void* stream) {
+    if (!h) return ALS_ERR_ARG;
+    h->stream = reinterpret_cast<cudaStream_t>(stream);
+    return ALS_OK;
+}
+
+int als_get_options(const als_handle* h, als_options* o) {
+    if (!h || !o) return ALS_ERR_ARG;
+    *o = h->opt;
+    return ALS_OK;
+}
+
+int als_prepare(als_handle* h, const als_csr* R) {
+    if (!h) return ALS_ERR_ARG;
+    int rc = check_csr(h, R);
+    if (rc) return rc;
+    Plan* pl = nullptr;
+    return build_plan(h, R, &pl);
+}
+
+int als_half_sweep(als_handle* h, const als_csr* R, const float* Y, float* X_out, int32_t* flags_out) {
+    if (!h) return ALS_ERR_ARG;
+    if (!X_out && R && R->n_rows > 0) return set_err(h, ALS_ERR_ARG, "X_out is null");
+    return dispatch_side(h, R, Y, 0, X_out, flags_out, nullptr, nullptr, nullptr);
+}
+
+int als_select(als_handle* h, const als_csr* R, const float* Y, uint32_t* masks_out) {
+    if (!h) return ALS_ERR_ARG;
+    if (!masks_out && R && R->nnz > 0) return set_err(h, ALS_ERR_ARG, "masks_out is null");
+    return dispatch_side(h, R, Y, 2, nullptr, nullptr, masks_out, nullptr, nullptr);
+}
+
+int als_assemble(als_handle* h, const als_csr* R, const float* Y, float* G_out, float* b_out) {
+    if (!h) return ALS_ERR_ARG;
+    if ((!G_out || !b_out) && R && R->n_rows > 0) return set_err(h, ALS_ERR_ARG, "G_out/b_out is null");
+    return dispatch_side(h, R, Y, 1, nullptr, nullptr, nullptr, G_out, b_out);
+}
+
+int als_solve(als_handle* h, int64_t n_rows, const float* G, const float* b, float* X_out, int32_t* flags_out) {
+    if (!h) return ALS_ERR_ARG;
+    if (n_rows < 0 || n_rows > 0x7fffffff) return set_err(h, ALS_ERR_ARG, "bad n_rows");
+    if (n_rows == 0) return ALS_OK;
+    if (!G || !b || !X_out) return set_err(h, ALS_ERR_ARG, "null buffer");
+    switch (padded_width(h->opt.n_f)) {
+        case 8: return solve_systems<8>(h, n_rows, G, b, X_out, flags_out);
+        case 16: return solve_systems<16>(h, n_rows, G, b, X_out, flags_out);
+        case 32: return solve_systems<32>(h, n_rows, G, b, X_out, flags_out);
+        default: return set_err(h, ALS_ERR_UNSUPPORTED, "n_f not supported");
+    }
+}
+
+int als_eval_sse(als_handle* h, int64_t n, const int32_t* iu, const int32_t* im, const float* r, const float* U,
+                 const float* M, double* sse_host) {
+    if (!h || !sse_host) return ALS_ERR_ARG;
+    if (n < 0) return set_err(h, ALS_ERR_ARG, "negative count");
+    if (n == 0) {
+        *sse_host = 0.0;
+        return ALS_OK;
+    }
+    if (!iu || !im || !r || !U || !M) return set_err(h, ALS_ERR_ARG, "null buffer");
+    cudaStream_t st = h->stream;
+    ALS_LAUNCH(h, "sse", als::k_sse<<<als::kEvalBlocks, als::kEvalThreads, 0, st>>>(n, iu, im, r, U, M, h->opt.n_f, eval_partials(h)));
+    ALS_LAUNCH(h, "sum_partials", als::k_sum_partials<<<1, 32, 0, st>>>(eval_partials(h), als::kEvalBlocks, eval_out(h)));
+    ALS_CUDA(h, cudaMemcpyAsync(sse_host, eval_out(h), sizeof(double), cudaMemcpyDeviceToHost, st));
+    ALS_CUDA(h, cudaStreamSynchronize(st));
+    return ALS_OK;
+}
+
+int als_eval_sse_async(als_handle* h, int64_t n, const int32_t* iu, const int32_t* im, const float* r,
+                       const float* U, const float* M, double* sse_dev) {
+    if (!h || !sse_dev) return ALS_ERR_ARG;
+    if (n < 0) return set_err(h, ALS_ERR_ARG, "negative count");
+    if (n > 0 && (!iu || !im || !r || !U || !M)) return set_err(h, ALS_ERR_ARG, "null buffer");
+    cudaStream_t st = h->stream;
+    if (n == 0) {
+        ALS_CUDA(h, cudaMemsetAsync(sse_dev, 0, sizeof(double), st));
+        return ALS_OK;
+    }
+    ALS_LAUNCH(h, "sse", als::k_sse<<<als::kEvalBlocks, als::kEvalThreads, 0, st>>>(n, iu, im, r, U, M, h->opt.n_f,
+                                                                                   eval_partials(h)));
+    ALS_LAUNCH(h, "sum_partials", als::k_sum_partials<<<1, 32, 0, st>>>(eval_partials(h), als::kEvalBlocks, sse_dev));
+    return ALS_OK;
+}
+
+int als_profile(als_handle* h, int enable) {
+    if (!h) return ALS_ERR_ARG;
+    ALS_CUDA(h, cudaStreamSynchronize(h->stream));
+    for (auto& t : h->timed) {
+        h->event_pool.push_back(t.start);
+        h->event_pool.push_back(t.stop);
+    }
+    h->timed.clear();
+    h->profiling = enable != 0;
+    return ALS_OK;
+}
+
+int als_kernel_time(als_handle* h, const char* name, double* ms_host, int64_t* launches_host) {
+    if (!h || !ms_host) return ALS_ERR_ARG;
+    ALS_CUDA(h, cudaStreamSynchronize(h->stream));
+    double total = 0.0;
+    int64_t count = 0;
+    for (auto& t : h->timed) {
+        if (name && std::strcmp(name, t.family) != 0) continue;
+        float ms = 0.f;
+        ALS_CUDA(h, cudaEventElapsedTime(&ms, t.start, t.stop));
+        total += ms;
+        ++count;
+    }
+    *ms_host = total;
+    if (launches_host) *launches_host = count;
+    return ALS_OK;
+}
+
+int als_get_report(als_handle* h, als_report* rep) {
+    if (!h || !rep) return ALS_ERR_ARG;
+    Counters c;
+    ALS_CUDA(h, cudaMemcpyAsync(&c, counters(h), sizeof c, cudaMemcpyDeviceToHost, h->stream));
+    ALS_CUDA(h, cudaStreamSynchronize(h->stream));
+    std::memset(rep, 0, sizeof *rep);
+    rep->rows_flagged = (int64_t)c.flagged;
+    rep->rows_singular = (int64_t)c.singular;
+    float mr;
+    std::memcpy(&mr, &c.max_ratio_bits, sizeof mr);
+    rep->max_pivot_ratio = mr;
+    rep->test_rmse = NAN;
+    rep->objective = NAN;
+    return ALS_OK;
+}
+
+int als_sweep(als_handle* h, const als_csr* Ru, const als_csr* Ri, float* U, float* M) {
+    if (!h) return ALS_ERR_ARG;
+    int rc = als_half_sweep(h, Ru, M, U, nullptr);
+    if (rc) return rc;
+    return als_half_sweep(h, Ri, U, M, nullptr);
+}
+
+int als_fit(als_handle* h, const als_csr* Ru, const als_csr* Ri, int sweeps, float* U, float* M, int64_t n_test,
+            const int32_t* tu, const int32_t* tm, const float* tr, als_report* rep) {
+    if (!h) return ALS_ERR_ARG;
+    if (sweeps < 0) return set_err(h, ALS_ERR_ARG, "negative sweep count");
+    if (!Ru || !Ri) return set_err(h, ALS_ERR_ARG, "null rating structure");
+    if (Ru->n_rows != Ri->n_cols || Ru->n_cols != Ri->n_rows || Ru->nnz != Ri->nnz)
+        return set_err(h, ALS_ERR_ARG, "user and item sides do not describe the same matrix");
+    for (int t = 0; t < sweeps; ++t) {
+        int rc = als_sweep(h, Ru, Ri, U, M);
+        if (rc) return rc;
+    }
+    if (rep) {
+        int rc = als_get_report(h, rep);
+        if (rc) return rc;
+        rep->sweeps_done = sweeps;
+        if (n_test > 0) {
+            double sse = 0.0;
+            rc = als_eval_sse(h, n_test, tu, tm, tr, U, M, &sse);
+            if (rc) return rc;
+            rep->test_rmse = std::sqrt(sse / (double)n_test);
+        }
+    }
+    return ALS_OK;
+}
+
+int als_fit_host(als_handle* h, int64_t n_u, int64_t n_m, int64_t nnz, const int64_t* uip, const int32_t* uix,
+                 const float* uv, const int64_t* iip, const int32_t* iix, const float* iv, int sweeps, float* U_host,
+                 float* M_host, int64_t n_test, const int32_t* tu, const int32_t* tm, const float* tr,
+                 als_report* rep) {
+    if (!h) return ALS_ERR_ARG;
+    if (n_u < 0 || n_m < 0 || nnz < 0 || n_test < 0) return set_err(h, ALS_ERR_ARG, "negative size");
+    if (!uip || !iip || !U_host || !M_host) return set_err(h, ALS_ERR_ARG, "null host buffer");
+    const int f = h->opt.n_f;
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t s_uip = al((n_u + 1) * 8), s_iip = al((n_m + 1) * 8), s_ix = al(nnz * 4), s_v = al(nnz * 4);
+    const size_t s_U = al(n_u * f * 4), s_M = al(n_m * f * 4), s_t = al(n_test * 4);
+    const size_t total = s_uip + s_iip + 2 * s_ix + 2 * s_v + s_U + s_M + 3 * s_t;
+    int rc = ensure(h, h->host_in, total);
+    if (rc) return rc;
+    char* base = reinterpret_cast<char*>(h->host_in.p);
+    auto take = [&](size_t b) { char* p = base; base += b; return p; };
+    int64_t* d_uip = (int64_t*)take(s_uip);
+    int64_t* d_iip = (int64_t*)take(s_iip);
+    int32_t* d_uix = (int32_t*)take(s_ix);
+    int32_t* d_iix = (int32_t*)take(s_ix);
+    float* d_uv = (float*)take(s_v);
+    float* d_iv = (float*)take(s_v);
+    float* d_U = (float*)take(s_U);
+    float* d_M = (float*)take(s_M);
+    int32_t* d_tu = (int32_t*)take(s_t);
+    int32_t* d_tm = (int32_t*)take(s_t);
+    float* d_tr = (float*)take(s_t);
+    cudaStream_t st = h->stream;
+    ALS_CUDA(h, cudaMemcpyAsync(d_uip, uip, (n_u + 1) * 8, cudaMemcpyHostToDevice, st));
+    ALS_CUDA(h, cudaMemcpyAsync(d_iip, iip, (n_m + 1) * 8, cudaMemcpyHostToDevice, st));
+    if (nnz > 0) {
+        ALS_CUDA(h, cudaMemcpyAsync(d_uix, uix, nnz * 4, cudaMemcpyHostToDevice, st));
+        ALS_CUDA(h, cudaMemcpyAsync(d_iix, iix, nnz * 4, cudaMemcpyHostToDevice, st));
+        ALS_CUDA(h, cudaMemcpyAsync(d_uv, uv, nnz * 4, cudaMemcpyHostToDevice, st));
+        ALS_CUDA(h, cudaMemcpyAsync(d_iv, iv, nnz * 4, cudaMemcpyHostToDevice, st));
+    }
+    ALS_CUDA(h, cudaMemcpyAsync(d_M, M_host, n_m * f * 4, cudaMemcpyHostToDevice, st));
+    if (n_test > 0) {
+        ALS_CUDA(h, cudaMemcpyAsync(d_tu, tu, n_test * 4, cudaMemcpyHostToDevice, st));
+        ALS_CUDA(h, cudaMemcpyAsync(d_tm, tm, n_test * 4, cudaMemcpyHostToDevice, st));
+        ALS_CUDA(h, cudaMemcpyAsync(d_tr, tr, n_test * 4, cudaMemcpyHostToDevice, st));
+    }
+    als_csr Ru{n_u, n_m, nnz, d_uip, d_uix, d_uv};
+    als_csr Ri{n_m, n_u, nnz, d_iip, d_iix, d_iv};
+    als_report local;
+    rc = als_fit(h, &Ru, &Ri, sweeps, d_U, d_M, n_test, d_tu, d_tm, d_tr, rep ? rep : &local);
+    if (rc) return rc;
+    ALS_CUDA(h, cudaMemcpyAsync(U_host, d_U, n_u * f * 4, cudaMemcpyDeviceToHost, st));
+    ALS_CUDA(h, cudaMemcpyAsync(M_host, d_M, n_m * f * 4, cudaMemcpyDeviceToHost, st));
+    ALS_CUDA(h, cudaStreamSynchronize(st));
+    // The device copies of the structure are reused by later calls only if
+    // they hold the same data, which this call cannot know: drop their plans.
+    h->plans.erase(std::remove_if(h->plans.begin(), h->plans.end(),
+                                  [&](const Plan& p) {
+                                      bool mine = p.indptr == d_uip || p.indptr == d_iip;
+                                      if (mine) cudaFree(p.d_lists);
+                                      return mine;
+                                  }),
+                   h->plans.end());
+    return ALS_OK;
+}
+
+int64_t als_workspace_bytes(const als_handle* h) {
+    if (!h) return 0;
+    int64_t b = (int64_t)(h->g_aug.bytes + h->misc.bytes + h->host_in.bytes);
+    for (const auto& p : h->plans) b += (int64_t)(p.n_warp + p.n_cta) * 4;
+    return b;
+}
+
+int64_t als_launch_count(const als_handle* h) { return h ? h->launches : 0; }
+
+const char* als_status_string(int s) {
+    switch (s) {
+        case ALS_OK: return "ok";
+        case ALS_ERR_ARG: return "invalid argument";
+        case ALS_ERR_CSR: return "invalid rating structure (indptr/indices)";
+        case ALS_ERR_NONFINITE: return "non-finite rating value";
+        case ALS_ERR_CUDA: return "CUDA runtime error";
+        case ALS_ERR_TIMEOUT: return "device wait timed out";
+        case ALS_ERR_OOM: return "device allocation failed";
+        case ALS_ERR_DEVICE_BOUNDS: return "device bounds check fired";
+        case ALS_ERR_UNSUPPORTED: return "unsupported option combination";
+        default: return "unknown status";
+    }
+}
+
+const char* als_last_error(const als_handle* h) { return h ? h->last_error.c_str() : "null handle"; }
+
+}  // extern "C"

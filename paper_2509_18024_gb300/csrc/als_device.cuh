@@ -1,0 +1,219 @@
+// Device-side building blocks of the core-elements ALS half-sweep (sm_103a).
+//
+// Notation follows the paper: a row i of one side has n_i observations I_i;
+// its design slice is X = Y[I_i] (n_i x n_f) with Y the other side's factor;
+// CES (Algorithm 1) keeps, in each column a of X, the s_i = floor(n_i r)
+// entries of largest |x_ka| (ties: lower position k first); Eq. (core_ui)
+// solves (X*^T X + lambda n_i E) x_i = X*^T r_i.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace als {
+
+enum { GRAM_ASYM = 0, GRAM_SYM = 1, GRAM_FULL = 2 };
+enum { REG_WEIGHTED = 0, REG_PLAIN = 1 };
+enum { FLAG_RATIO = 1, FLAG_SINGULAR = 2 };
+
+constexpr unsigned kFull = 0xffffffffu;
+
+struct Params {
+    int f;               // rank n_f (<= F, the compile-time padded width)
+    float lambda;
+    double budget;       // r
+    long long min_keep;  // 0 = off
+    int reg_mode;
+    int gram_mode;
+    float ratio_max;     // pivot-ratio flag threshold
+};
+
+struct Side {
+    const int64_t* indptr;
+    const int32_t* indices;
+    const float* values;
+    const float* Y;      // other side's factor, n_cols x f
+    int64_t n_rows;
+    int64_t n_cols;
+};
+
+// Report counters of one half-sweep (device resident).
+struct Counters {
+    unsigned long long flagged;
+    unsigned long long singular;
+    unsigned int max_ratio_bits;  // float bits of the largest finite pivot ratio
+    unsigned int error;           // device-side error word (0 = none)
+};
+
+// |x| as an order-preserving unsigned key: for finite floats the unsigned
+// order of the sign-cleared bit pattern is the order of |x|; -0 and +0 tie.
+__device__ __forceinline__ uint32_t mag_key(float x) { return __float_as_uint(x) & 0x7fffffffu; }
+
+// s_i = floor(n_i * r) in IEEE double (the same expression as the oracle),
+// optionally raised to min_keep; n_i for the full update.
+__device__ __forceinline__ long long row_budget(long long n, const Params& p) {
+    if (p.gram_mode == GRAM_FULL) return n;
+    double prod = (double)n * p.budget;
+    long long s = (long long)floor(prod);
+    if (s > n) s = n;
+    if (s < 0) s = 0;
+    if (p.min_keep > 0 && s < p.min_keep) s = p.min_keep < n ? p.min_keep : n;
+    return s;
+}
+
+// Regulariser added on the diagonal: lambda n_i (weighted) or lambda.
+__device__ __forceinline__ float row_reg(long long n, const Params& p) {
+    return p.reg_mode == REG_PLAIN ? p.lambda : (float)((double)p.lambda * (double)n);
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+__device__ __forceinline__ unsigned lanemask_gt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_gt;" : "=r"(m));
+    return m;
+}
+
+// Warp-wide CES on one column of a slice with n <= 32 elements, element k
+// held by lane k. Returns the keep mask (bit k). Exact: the s largest keys,
+// equal keys taken from the lowest lanes. When s <= n - s it extracts maxima
+// s times at most; otherwise it removes the n - s smallest (equal keys leave
+// from the highest lanes), which yields the same set.
+__device__ __forceinline__ unsigned warp_ces_column(uint32_t key, int n, int s) {
+    const int lane = threadIdx.x & 31;
+    const unsigned valid = (n >= 32) ? kFull : ((1u << n) - 1u);
+    if (s <= 0) return 0u;
+    if (s >= n) return valid;
+    if (2 * s <= n) {
+        // key + 1 never overflows (keys <= 0x7fffffff); removed lanes hold 0.
+        uint32_t k1 = (lane < n) ? key + 1u : 0u;
+        unsigned sel = 0u;
+        int need = s;
+        // Each round takes at least one of <= 32 elements: at most 32 rounds.
+        for (int round = 0; need > 0 && round < 32; ++round) {
+            uint32_t m = __reduce_max_sync(kFull, k1);
+            unsigned eq = __ballot_sync(kFull, k1 == m);
+            unsigned take;
+            if (__popc(eq) <= need) {
+                take = eq;
+            } else {
+                bool mine = ((eq >> lane) & 1u) && (__popc(eq & lanemask_lt()) < need);
+                take = __ballot_sync(kFull, mine);
+            }
+            sel |= take;
+            need -= __popc(take);
+            if ((take >> lane) & 1u) k1 = 0u;
+        }
+        return sel;
+    } else {
+        uint32_t k2 = (lane < n) ? key : 0xffffffffu;
+        unsigned excl = 0u;
+        int need = n - s;
+        // Each round takes at least one of <= 32 elements: at most 32 rounds.
+        for (int round = 0; need > 0 && round < 32; ++round) {
+            uint32_t m = __reduce_min_sync(kFull, k2);
+            unsigned eq = __ballot_sync(kFull, k2 == m) & valid;
+            unsigned take;
+            if (__popc(eq) <= need) {
+                take = eq;
+            } else {
+                bool mine = ((eq >> lane) & 1u) && (__popc(eq & lanemask_gt()) < need);
+                take = __ballot_sync(kFull, mine);
+            }
+            excl |= take;
+            need -= __popc(take);
+            if ((take >> lane) & 1u) k2 = 0xffffffffu;
+        }
+        return valid & ~excl;
+    }
+}
+
+// Warp-cooperative solve of one F x F system held row-per-lane: lane i < F
+// holds row i of A in v[0..F-1] and b_i in rhs. Gaussian elimination; with
+// `pivot` true the pivot of step k is the remaining row with the largest
+// |a_ik| (lowest lane on ties) - partial pivoting without moving data - else
+// the diagonal (the symmetric positive definite modes, where the pivots are
+// the squared Cholesky diagonal L_kk^2). Rows a >= f are padding (identity).
+// Returns the solution component of this lane's column (lane < F) through
+// x_lane; flags and the pivot ratio max/min over the first f pivots.
+template <int F>
+__device__ __forceinline__ void warp_solve(float (&v)[F], float rhs, int f, bool pivot, float ratio_max,
+                                           float& x_lane, int& flags, float& ratio) {
+    const int lane = threadIdx.x & 31;
+    bool active = lane < F;
+    int ord = -1;  // elimination step at which this lane's row was the pivot
+    float pmax = 0.f, pmin = __int_as_float(0x7f800000);
+    bool singular = false;
+#pragma unroll
+    for (int k = 0; k < F; ++k) {
+        int bl;
+        if (pivot) {
+            float best = active ? fabsf(v[k]) : -1.f;
+            bl = lane;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                float ob = __shfl_xor_sync(kFull, best, o);
+                int ol = __shfl_xor_sync(kFull, bl, o);
+                if (ob > best || (ob == best && ol < bl)) {
+                    best = ob;
+                    bl = ol;
+                }
+            }
+        } else {
+            bl = k;
+        }
+        float pv = __shfl_sync(kFull, v[k], bl);
+        float apv = pivot ? fabsf(pv) : pv;
+        if (k < f) {
+            if (!(apv > 0.f)) singular = true;
+            pmax = fmaxf(pmax, apv);
+            pmin = fminf(pmin, apv);
+        }
+        float l = (active && lane != bl && pv != 0.f) ? v[k] / pv : 0.f;
+#pragma unroll
+        for (int j = k + 1; j < F; ++j) {
+            float pj = __shfl_sync(kFull, v[j], bl);
+            v[j] = fmaf(-l, pj, v[j]);
+        }
+        float pr = __shfl_sync(kFull, rhs, bl);
+        rhs = fmaf(-l, pr, rhs);
+        if (lane == bl) {
+            active = false;
+            ord = k;
+        }
+    }
+    // Back substitution in pivot order: the row eliminated at step k holds
+    // the k-th row of the upper factor.
+    float out = 0.f;
+#pragma unroll
+    for (int k = F - 1; k >= 0; --k) {
+        unsigned owner = __ballot_sync(kFull, ord == k);
+        int src = __ffs(owner) - 1;
+        float mine = (ord == k) ? rhs / v[k] : 0.f;
+        float xk = __shfl_sync(kFull, mine, src);
+        if (lane == k) out = xk;
+        rhs = fmaf(-v[k], xk, rhs);
+    }
+    flags = 0;
+    ratio = (f > 0) ? pmax / pmin : 1.f;
+    if (singular) {
+        flags = FLAG_SINGULAR | FLAG_RATIO;
+        out = 0.f;
+        ratio = __int_as_float(0x7f800000);
+    } else if (!(ratio <= ratio_max)) {
+        flags = FLAG_RATIO;
+    }
+    x_lane = out;
+}
+
+__device__ __forceinline__ void record_flags(Counters* c, int flags, float ratio) {
+    if (flags & FLAG_RATIO) atomicAdd(&c->flagged, 1ull);
+    if (flags & FLAG_SINGULAR) atomicAdd(&c->singular, 1ull);
+    else if (ratio > 0.f && ratio < __int_as_float(0x7f800000))
+        atomicMax(&c->max_ratio_bits, __float_as_uint(ratio));
+}
+
+}  // namespace als

@@ -19,14 +19,56 @@ using als::Counters;
 using als::Params;
 using als::Side;
 
-// Row plan of one side: rows bucketed by length (warp rows n_i <= 32, CTA
-// rows longer, sorted by length descending so the longest start first).
+// Row plan of one side: rows bucketed by length - warp rows (n_i <= 32),
+// three CTA-resident capacities (<= 128, <= 512, <= 1024) and split rows
+// (> 1024, cut into 512-position chunks); each CTA bucket sorted by length
+// descending so the longest start first.
+constexpr int kBucketCap[3] = {128, 512, 1024};
+
 struct Plan {
     const int64_t* indptr = nullptr;
     int64_t n_rows = 0, nnz = 0, n_cols = 0;
-    int n_warp = 0, n_cta = 0;
+    int F = 0;
+    int n_warp = 0;
+    int n_bucket[3] = {0, 0, 0};
+    int n_slots = 0, n_chunks = 0;
     int64_t max_len = 0;
-    int32_t* d_lists = nullptr;  // [warp rows | cta rows]
+    int32_t* d_lists = nullptr;  // [warp | bucket0 | bucket1 | bucket2 | split rows | c_begin | ch_slot | ch_start]
+    void* d_split = nullptr;     // split-row selection state and scratch
+    int off_bucket(int b) const {
+        int o = n_warp;
+        for (int q = 0; q < b; ++q) o += n_bucket[q];
+        return o;
+    }
+    int off_split() const { return off_bucket(3); }
+    int n_cta_like() const { return n_bucket[0] + n_bucket[1] + n_bucket[2] + n_slots; }
+};
+
+void free_plan(Plan& p) {
+    if (p.d_lists) cudaFree(p.d_lists);
+    if (p.d_split) cudaFree(p.d_split);
+    p.d_lists = nullptr;
+    p.d_split = nullptr;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Layout of Plan::d_split for width F.
+struct SplitLayout {
+    size_t P, Mk, need, cut, done, ghist, eqc, part, total;
+    SplitLayout(int n_slots, int n_chunks, int F) {
+        size_t o = 0;
+        const size_t sc = (size_t)std::max(n_slots, 1) * F * 4;
+        P = o; o += align256(sc);
+        Mk = o; o += align256(sc);
+        need = o; o += align256(sc);
+        cut = o; o += align256(sc);
+        done = o; o += align256(sc);
+        ghist = o; o += align256(sc * 256);
+        eqc = o; o += align256((size_t)std::max(n_chunks, 1) * F * 4);
+        part = o; o += align256((size_t)std::max(n_chunks, 1) * F * (F + 1) * 4);
+        total = o;
+    }
 };
 
 struct DevBuf {
@@ -212,40 +254,66 @@ int build_plan(als_handle* h, const als_csr* R, Plan** out) {
     if (err & 2u) return set_err(h, ALS_ERR_CSR, "indices out of range, unsorted or duplicated inside a row");
     if (err & 4u) return set_err(h, ALS_ERR_NONFINITE, "non-finite rating value");
 
-    std::vector<int32_t> warp_rows, cta_rows;
+    const int F = padded_width(h->opt.n_f);
+    std::vector<int32_t> warp_rows, bucket[3], split_rows;
     int64_t max_len = 0;
     for (int64_t i = 0; i < R->n_rows; ++i) {
-        int64_t len = indptr[i + 1] - indptr[i];
+        const int64_t len = indptr[i + 1] - indptr[i];
         max_len = std::max(max_len, len);
         if (len <= als::kWarpRowMax) warp_rows.push_back((int32_t)i);
-        else cta_rows.push_back((int32_t)i);
+        else if (len <= kBucketCap[0]) bucket[0].push_back((int32_t)i);
+        else if (len <= kBucketCap[1]) bucket[1].push_back((int32_t)i);
+        else if (len <= kBucketCap[2]) bucket[2].push_back((int32_t)i);
+        else split_rows.push_back((int32_t)i);
     }
-    std::stable_sort(cta_rows.begin(), cta_rows.end(), [&](int32_t a, int32_t b) {
-        return indptr[a + 1] - indptr[a] > indptr[b + 1] - indptr[b];
-    });
+    auto longer = [&](int32_t a, int32_t b) { return indptr[a + 1] - indptr[a] > indptr[b + 1] - indptr[b]; };
+    for (auto& v : bucket) std::stable_sort(v.begin(), v.end(), longer);
+    std::stable_sort(split_rows.begin(), split_rows.end(), longer);
+    std::vector<int32_t> c_begin(1, 0), ch_slot, ch_start;
+    for (size_t q = 0; q < split_rows.size(); ++q) {
+        const int64_t len = indptr[split_rows[q] + 1] - indptr[split_rows[q]];
+        for (int64_t st = 0; st < len; st += als::kSplitChunk) {
+            ch_slot.push_back((int32_t)q);
+            ch_start.push_back((int32_t)st);
+        }
+        c_begin.push_back((int32_t)ch_slot.size());
+    }
     Plan p;
     p.indptr = R->indptr;
     p.n_rows = R->n_rows;
     p.nnz = R->nnz;
     p.n_cols = R->n_cols;
+    p.F = F;
     p.n_warp = (int)warp_rows.size();
-    p.n_cta = (int)cta_rows.size();
+    for (int q = 0; q < 3; ++q) p.n_bucket[q] = (int)bucket[q].size();
+    p.n_slots = (int)split_rows.size();
+    p.n_chunks = (int)ch_slot.size();
     p.max_len = max_len;
     std::vector<int32_t> lists(warp_rows);
-    lists.insert(lists.end(), cta_rows.begin(), cta_rows.end());
-    size_t bytes = std::max<size_t>(lists.size(), 1) * sizeof(int32_t);
-    cudaError_t e = cudaMalloc(&p.d_lists, bytes);
+    for (auto& v : bucket) lists.insert(lists.end(), v.begin(), v.end());
+    lists.insert(lists.end(), split_rows.begin(), split_rows.end());
+    lists.insert(lists.end(), c_begin.begin(), c_begin.end());
+    lists.insert(lists.end(), ch_slot.begin(), ch_slot.end());
+    lists.insert(lists.end(), ch_start.begin(), ch_start.end());
+    cudaError_t e = cudaMalloc(&p.d_lists, lists.size() * sizeof(int32_t));
     if (e != cudaSuccess) {
         cudaGetLastError();
         return set_err(h, ALS_ERR_OOM, "cudaMalloc(plan) failed");
     }
-    if (!lists.empty()) {
-        ALS_CUDA(h, cudaMemcpyAsync(p.d_lists, lists.data(), lists.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        ALS_CUDA(h, cudaStreamSynchronize(st));
+    const SplitLayout L(p.n_slots, p.n_chunks, F);
+    e = cudaMalloc(&p.d_split, L.total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_plan(p);
+        return set_err(h, ALS_ERR_OOM, "cudaMalloc(split state, %zu bytes) failed", L.total);
     }
+    ALS_CUDA(h, cudaMemcpyAsync(p.d_lists, lists.data(), lists.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    // The split histograms start (and stay between passes) at zero.
+    ALS_CUDA(h, cudaMemsetAsync(reinterpret_cast<char*>(p.d_split) + L.ghist, 0, L.eqc - L.ghist, st));
+    ALS_CUDA(h, cudaStreamSynchronize(st));
     // Keep a small bounded cache of plans.
     if (h->plans.size() >= 8) {
-        cudaFree(h->plans.front().d_lists);
+        free_plan(h->plans.front());
         h->plans.erase(h->plans.begin());
     }
     h->plans.push_back(p);
@@ -253,16 +321,55 @@ int build_plan(als_handle* h, const als_csr* R, Plan** out) {
     return ALS_OK;
 }
 
-template <int F>
-size_t cta_smem_bytes() {
-    return sizeof(als::CtaRowSmem<F>);
+template <int F, int NS>
+int launch_cta_bucket(als_handle* h, const Side& side, const Params& p, const int32_t* list, int count, int mode,
+                      float* G_aug, uint32_t* masks_out) {
+    if (count == 0) return ALS_OK;
+    const size_t smem = sizeof(als::CtaSmem<F, NS>);
+    ALS_CUDA(h, cudaFuncSetAttribute(als::k_cta_rows<F, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ALS_LAUNCH(h, "cta_rows", als::k_cta_rows<F, NS><<<count, als::kCtaThreads, smem, h->stream>>>(
+                                  side, p, list, count, mode, G_aug, masks_out));
+    return ALS_OK;
 }
 
 template <int F>
-int configure_kernels(als_handle* h) {
-    // Per-function attribute of the current device; cheap to repeat.
-    ALS_CUDA(h, cudaFuncSetAttribute(als::k_cta_rows<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)cta_smem_bytes<F>()));
+int launch_split(als_handle* h, const Plan& pl, const Side& side, const Params& p, int mode, float* G_aug,
+                 uint32_t* masks_out) {
+    if (pl.n_slots == 0) return ALS_OK;
+    cudaStream_t st = h->stream;
+    const int32_t* base = pl.d_lists;
+    als::SplitPlan sp;
+    sp.row = base + pl.off_split();
+    sp.c_begin = sp.row + pl.n_slots;
+    sp.ch_slot = sp.c_begin + pl.n_slots + 1;
+    sp.ch_start = sp.ch_slot + pl.n_chunks;
+    sp.n_slots = pl.n_slots;
+    sp.n_chunks = pl.n_chunks;
+    const SplitLayout L(pl.n_slots, pl.n_chunks, F);
+    char* mem = reinterpret_cast<char*>(pl.d_split);
+    als::SplitState ss;
+    ss.P = reinterpret_cast<uint32_t*>(mem + L.P);
+    ss.Mk = reinterpret_cast<uint32_t*>(mem + L.Mk);
+    ss.need = reinterpret_cast<int32_t*>(mem + L.need);
+    ss.cut = reinterpret_cast<int32_t*>(mem + L.cut);
+    ss.done = reinterpret_cast<int32_t*>(mem + L.done);
+    ss.ghist = reinterpret_cast<uint32_t*>(mem + L.ghist);
+    ss.eqc = reinterpret_cast<int32_t*>(mem + L.eqc);
+    ss.part = reinterpret_cast<float*>(mem + L.part);
+    const int sc = pl.n_slots * F;
+    ALS_LAUNCH(h, "split_init", als::k_split_init<F><<<(sc + 255) / 256, 256, 0, st>>>(side, p, sp, ss));
+    for (int pass = 0; pass < 4; ++pass) {
+        ALS_LAUNCH(h, "split_hist", als::k_split_hist<F><<<pl.n_chunks, als::kCtaThreads, 0, st>>>(side, p, sp, ss, pass));
+        ALS_LAUNCH(h, "split_scan", als::k_split_scan<F><<<(sc * 32 + 255) / 256, 256, 0, st>>>(sp, ss, pass));
+    }
+    ALS_LAUNCH(h, "split_eqcount", als::k_split_eqcount<F><<<pl.n_chunks, als::kCtaThreads, 0, st>>>(side, p, sp, ss));
+    ALS_LAUNCH(h, "split_cut", als::k_split_cut<F><<<(sc * 32 + 255) / 256, 256, 0, st>>>(side, p, sp, ss));
+    const size_t smem = sizeof(als::SplitGramSmem<F>);
+    ALS_CUDA(h, cudaFuncSetAttribute(als::k_split_gram<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ALS_LAUNCH(h, "split_gram", als::k_split_gram<F><<<pl.n_chunks, als::kCtaThreads, smem, st>>>(side, p, sp, ss, mode,
+                                                                                                 masks_out));
+    if (mode != 2)
+        ALS_LAUNCH(h, "split_reduce", als::k_split_reduce<F><<<pl.n_slots, als::kCtaThreads, 0, st>>>(side, p, sp, ss, G_aug));
     return ALS_OK;
 }
 
@@ -270,36 +377,51 @@ int configure_kernels(als_handle* h) {
 template <int F>
 int run_side(als_handle* h, const Plan& pl, const Side& side, int mode, float* X_out, int32_t* flags_out,
              uint32_t* masks_out, float* G_out, float* b_out) {
-    int rc = configure_kernels<F>(h);
-    if (rc) return rc;
     cudaStream_t st = h->stream;
     Params p = make_params(h->opt);
-    const int32_t* warp_list = pl.d_lists;
-    const int32_t* cta_list = pl.d_lists + pl.n_warp;
-    const int n_lists_max = std::max(pl.n_warp, pl.n_cta);
-    if (mode == 1) {
-        rc = ensure(h, h->g_aug, (size_t)std::max(n_lists_max, 1) * F * (F + 1) * sizeof(float));
-    } else {
-        rc = ensure(h, h->g_aug, (size_t)std::max(pl.n_cta, 1) * F * (F + 1) * sizeof(float));
-    }
+    const int n_aug = std::max(pl.n_cta_like(), mode == 1 ? pl.n_warp : 0);
+    int rc = ensure(h, h->g_aug, (size_t)std::max(n_aug, 1) * F * (F + 1) * sizeof(float));
     if (rc) return rc;
     float* G_aug = reinterpret_cast<float*>(h->g_aug.p);
-    if (pl.n_cta > 0) {
-        ALS_LAUNCH(h, "cta_rows", als::k_cta_rows<F><<<pl.n_cta, als::kCtaThreads, cta_smem_bytes<F>(), st>>>(side, p, cta_list, pl.n_cta,
-                                                                                  mode, G_aug, masks_out));
+    // Augmented systems: [split slots | bucket0 | bucket1 | bucket2] in G_aug.
+    float* aug_split = G_aug;
+    float* aug_b0 = aug_split + (size_t)pl.n_slots * F * (F + 1);
+    float* aug_b1 = aug_b0 + (size_t)pl.n_bucket[0] * F * (F + 1);
+    float* aug_b2 = aug_b1 + (size_t)pl.n_bucket[1] * F * (F + 1);
+    rc = launch_split<F>(h, pl, side, p, mode, aug_split, masks_out);
+    if (rc) return rc;
+    const int32_t* lists = pl.d_lists;
+    rc = launch_cta_bucket<F, 1024>(h, side, p, lists + pl.off_bucket(2), pl.n_bucket[2], mode, aug_b2, masks_out);
+    if (rc) return rc;
+    rc = launch_cta_bucket<F, 512>(h, side, p, lists + pl.off_bucket(1), pl.n_bucket[1], mode, aug_b1, masks_out);
+    if (rc) return rc;
+    rc = launch_cta_bucket<F, 128>(h, side, p, lists + pl.off_bucket(0), pl.n_bucket[0], mode, aug_b0, masks_out);
+    if (rc) return rc;
+    // Systems of the split and CTA rows, in G_aug order: split rows first,
+    // then buckets 0..2 (the lists are laid out in the same order apart from
+    // the split rows, which follow the buckets in the list array).
+    struct Seg { const int32_t* list; int count; float* aug; };
+    const Seg segs[4] = {{lists + pl.off_split(), pl.n_slots, aug_split},
+                         {lists + pl.off_bucket(0), pl.n_bucket[0], aug_b0},
+                         {lists + pl.off_bucket(1), pl.n_bucket[1], aug_b1},
+                         {lists + pl.off_bucket(2), pl.n_bucket[2], aug_b2}};
+    for (const Seg& sg : segs) {
+        if (sg.count == 0) continue;
         if (mode == 0) {
-            ALS_LAUNCH(h, "solve_rows", als::k_solve_rows<F><<<(pl.n_cta + 7) / 8, 256, 0, st>>>(G_aug, cta_list, pl.n_cta, p, X_out, flags_out,
-                                                                     counters(h)));
+            ALS_LAUNCH(h, "solve_rows", als::k_solve_rows<F><<<(sg.count + 7) / 8, 256, 0, st>>>(
+                                            sg.aug, sg.list, sg.count, p, X_out, flags_out, counters(h)));
         } else if (mode == 1) {
-            ALS_LAUNCH(h, "unpack_aug", als::k_unpack_aug<F><<<1024, 256, 0, st>>>(G_aug, cta_list, pl.n_cta, p.f, G_out, b_out));
+            ALS_LAUNCH(h, "unpack_aug", als::k_unpack_aug<F><<<1024, 256, 0, st>>>(sg.aug, sg.list, sg.count, p.f,
+                                                                                    G_out, b_out));
         }
     }
     if (pl.n_warp > 0) {
-        ALS_LAUNCH(h, "warp_rows", als::k_warp_rows<F><<<(pl.n_warp + 7) / 8, 256, 0, st>>>(side, p, warp_list, pl.n_warp, mode, X_out,
-                                                                 flags_out, masks_out, G_aug, counters(h)));
-        if (mode == 1) {
-            ALS_LAUNCH(h, "unpack_aug", als::k_unpack_aug<F><<<1024, 256, 0, st>>>(G_aug, warp_list, pl.n_warp, p.f, G_out, b_out));
-        }
+        ALS_LAUNCH(h, "warp_rows", als::k_warp_rows<F><<<(pl.n_warp + 7) / 8, 256, 0, st>>>(
+                                       side, p, lists, pl.n_warp, mode, X_out, flags_out, masks_out, G_aug,
+                                       counters(h)));
+        if (mode == 1)
+            ALS_LAUNCH(h, "unpack_aug", als::k_unpack_aug<F><<<1024, 256, 0, st>>>(G_aug, lists, pl.n_warp, p.f,
+                                                                                    G_out, b_out));
     }
     return ALS_OK;
 }
@@ -390,7 +512,7 @@ int als_create(als_handle** out, const als_options* opt, void* stream) {
 int als_destroy(als_handle* h) {
     if (!h) return ALS_ERR_ARG;
     cudaStreamSynchronize(h->stream);
-    for (auto& p : h->plans) cudaFree(p.d_lists);
+    for (auto& p : h->plans) free_plan(p);
     for (auto& t : h->timed) {
         cudaEventDestroy(t.start);
         cudaEventDestroy(t.stop);
@@ -618,7 +740,7 @@ int als_fit_host(als_handle* h, int64_t n_u, int64_t n_m, int64_t nnz, const int
     h->plans.erase(std::remove_if(h->plans.begin(), h->plans.end(),
                                   [&](const Plan& p) {
                                       bool mine = p.indptr == d_uip || p.indptr == d_iip;
-                                      if (mine) cudaFree(p.d_lists);
+                                      if (mine) free_plan(const_cast<Plan&>(p));
                                       return mine;
                                   }),
                    h->plans.end());
@@ -628,7 +750,8 @@ int als_fit_host(als_handle* h, int64_t n_u, int64_t n_m, int64_t nnz, const int
 int64_t als_workspace_bytes(const als_handle* h) {
     if (!h) return 0;
     int64_t b = (int64_t)(h->g_aug.bytes + h->misc.bytes + h->host_in.bytes);
-    for (const auto& p : h->plans) b += (int64_t)(p.n_warp + p.n_cta) * 4;
+    for (const auto& p : h->plans)
+        b += (int64_t)SplitLayout(p.n_slots, p.n_chunks, p.F).total + (int64_t)(p.n_rows + 2 * p.n_chunks + p.n_slots + 1) * 4;
     return b;
 }
 

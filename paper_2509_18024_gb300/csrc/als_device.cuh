@@ -209,6 +209,76 @@ __device__ __forceinline__ void warp_solve(float (&v)[F], float rhs, int f, bool
     x_lane = out;
 }
 
+// ---------------------------------------------------------------------------
+// Exact radix select of the s-th largest key, 8 bits per pass from the top of
+// the magnitude key (bit 31 is always 0): pass 0 resolves the exponent
+// (bits 30..23), passes 1-3 the mantissa (22..15, 14..7, 6..0). After a pass
+// every key whose covered bits exceed the prefix P is kept; keys equal to P on
+// the covered bits form the open class, of which `need` are still kept.
+__device__ __forceinline__ int radix_shift(int pass) { return pass == 0 ? 23 : (pass == 1 ? 15 : (pass == 2 ? 7 : 0)); }
+__device__ __forceinline__ uint32_t radix_before(int pass) {
+    return pass == 0 ? 0u : (pass == 1 ? 0xff800000u : (pass == 2 ? 0xffff8000u : 0xffffff80u));
+}
+__device__ __forceinline__ uint32_t radix_after(int pass) {
+    return pass == 0 ? 0xff800000u : (pass == 1 ? 0xffff8000u : (pass == 2 ? 0xffffff80u : 0xffffffffu));
+}
+__device__ __forceinline__ uint32_t radix_digit(uint32_t key, int pass) { return (key >> radix_shift(pass)) & 0xffu; }
+
+struct BinPick {
+    int digit;         // bin holding the need-th largest key
+    uint32_t newneed;  // keys still to take inside that bin
+    uint32_t inbin;    // keys in that bin
+};
+
+// Warp-cooperative scan of 256 bins (any address space) from the top bin
+// down: the bin where the running count first reaches `need` (>= 1; the bins
+// must hold at least `need` keys in total).
+__device__ __forceinline__ BinPick warp_pick_bin(const uint32_t* bins, uint32_t need) {
+    const int lane = threadIdx.x & 31;
+    uint32_t c[8];
+    uint32_t lsum = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        c[q] = bins[lane * 8 + q];
+        lsum += c[q];
+    }
+    uint32_t incl = lsum;  // keys in bins of lanes >= this lane
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_down_sync(kFull, incl, o);
+        if (lane + o < 32) incl += t;
+    }
+    const uint32_t above = incl - lsum;
+    const unsigned ob = __ballot_sync(kFull, above < need && need <= incl);
+    const int L = __ffs(ob) - 1;
+    BinPick r{0, 0u, 0u};
+    if (lane == L) {
+        uint32_t cum = above;
+        bool found = false;
+#pragma unroll
+        for (int q = 7; q >= 0; --q) {
+            if (!found && cum + c[q] >= need) {
+                r.digit = lane * 8 + q;
+                r.newneed = need - cum;
+                r.inbin = c[q];
+                found = true;
+            }
+            if (!found) cum += c[q];
+        }
+    }
+    r.digit = __shfl_sync(kFull, r.digit, L < 0 ? 0 : L);
+    r.newneed = __shfl_sync(kFull, r.newneed, L < 0 ? 0 : L);
+    r.inbin = __shfl_sync(kFull, r.inbin, L < 0 ? 0 : L);
+    return r;
+}
+
+// Keep rule of one column after selection: (key & Mk) > P, or equal to P on
+// the covered bits and at a position below cut.
+__device__ __forceinline__ bool keep_rule(uint32_t key, uint32_t P, uint32_t Mk, int pos, int cut) {
+    const uint32_t kc = key & Mk;
+    return kc > P || (kc == P && pos < cut);
+}
+
 __device__ __forceinline__ void record_flags(Counters* c, int flags, float ratio) {
     if (flags & FLAG_RATIO) atomicAdd(&c->flagged, 1ull);
     if (flags & FLAG_SINGULAR) atomicAdd(&c->singular, 1ull);

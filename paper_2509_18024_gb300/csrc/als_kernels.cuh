@@ -1,15 +1,17 @@
 // Kernels of one Core-ALS half-sweep on CUDA cores (FP32), n_f <= 32.
 //
 // Rows are bucketed by length by the host planner:
-//   * k_warp_rows : n_i <= 32. One warp per row does CES (Algorithm 1),
-//                   the Gram assembly of Eq. (core_ui) and the solve, all in
-//                   registers and a warp-private shared-memory tile.
-//   * k_cta_rows  : n_i > 32. One CTA per row does CES by an exact radix
-//                   select over shared-memory histograms and the masked Gram
-//                   assembly; the augmented system [G | b] goes to the
-//                   workspace and k_solve_rows solves it (warp per row).
-//                   Rows up to kCtaResident elements are staged in shared
-//                   memory once; longer rows are streamed from L2 per pass.
+//   * k_warp_rows  : n_i <= 32. One warp per row does CES (Algorithm 1),
+//                    the Gram assembly of Eq. (core_ui) and the solve, all in
+//                    registers and a warp-private shared-memory tile.
+//   * k_cta_rows   : 32 < n_i <= 1024 (three capacity buckets). One CTA per
+//                    row stages the slice in shared memory once, selects by
+//                    an exact radix select and assembles the masked Gram.
+//   * k_split_*    : n_i > 1024. The row is cut into 512-element chunks, one
+//                    CTA each; the radix passes meet in per-row global
+//                    histograms and the chunk Grams are summed in chunk order.
+//   The augmented systems [G | b] of the CTA and split rows are solved by
+//   k_solve_rows (warp per row).
 #pragma once
 
 #include "als_device.cuh"
@@ -17,9 +19,6 @@
 namespace als {
 
 constexpr int kWarpRowMax = 32;
-constexpr int kCtaThreads = 256;
-constexpr int kCtaWarps = kCtaThreads / 32;
-constexpr int kCtaResident = 256;
 
 // ---------------------------------------------------------------------------
 // Warp per row (n_i <= 32).
@@ -146,260 +145,11 @@ __global__ void __launch_bounds__(256) k_warp_rows(Side side, Params p, const in
     }
 }
 
-// ---------------------------------------------------------------------------
-// CTA per row (n_i > 32).
-template <int F>
-struct CtaRowSmem {
-    float x[kCtaResident][F];
-    float r[kCtaResident];
-    int32_t idx[kCtaResident];
-    uint32_t mask[kCtaResident];
-    union {
-        uint32_t hist[F][256];
-        float Gp[kCtaWarps][F][F + 1];
-    } u;
-    uint32_t P[F];     // resolved high-bit prefix of the threshold key
-    uint32_t Mk[F];    // bits of the key covered by P
-    int32_t need[F];   // elements still to take inside the prefix class
-    int32_t cut[F];    // positional cut among keys equal to P (INT_MAX = none)
-    int32_t done[F];
-    int32_t active;
-};
+}  // namespace als
 
-template <int F>
-__device__ __forceinline__ void cta_stage(CtaRowSmem<F>& S, const Side& side, int f, int64_t lo, int c0, int cn) {
-    for (int k = threadIdx.x; k < cn; k += kCtaThreads) {
-        S.idx[k] = side.indices[lo + c0 + k];
-        S.r[k] = side.values[lo + c0 + k];
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < cn * F; e += kCtaThreads) {
-        const int k = e / F, a = e % F;
-        S.x[k][a] = (a < f) ? __ldg(side.Y + (int64_t)S.idx[k] * f + a) : 0.f;
-    }
-    __syncthreads();
-}
+#include "als_rows.cuh"
 
-template <int F>
-__global__ void __launch_bounds__(kCtaThreads) k_cta_rows(Side side, Params p, const int32_t* __restrict__ rows,
-                                                          int n_list, int mode, float* __restrict__ G_aug,
-                                                          uint32_t* __restrict__ masks_out) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    CtaRowSmem<F>& S = *reinterpret_cast<CtaRowSmem<F>*>(smem_raw);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int w = blockIdx.x;
-    if (w >= n_list) return;
-    const int f = p.f;
-    const int64_t i = rows[w];
-    const int64_t lo = side.indptr[i];
-    const int n = (int)(side.indptr[i + 1] - lo);
-    const bool resident = n <= kCtaResident;
-    const int s = (int)row_budget(n, p);
-    // Thread t always handles column a_t = t mod F (F divides the block size).
-    const int a_t = tid % F;
-    const int k0 = tid / F;
-    constexpr int kstep = kCtaThreads / F;
-
-    if (tid < F) {
-        const bool real = tid < f;
-        S.need[tid] = s;
-        S.cut[tid] = 0x7fffffff;
-        if (!real || s == 0) {  // keep nothing
-            S.P[tid] = 0xffffffffu;
-            S.Mk[tid] = 0xffffffffu;
-            S.cut[tid] = 0;
-            S.done[tid] = 1;
-        } else if (s >= n) {  // keep everything
-            S.P[tid] = 0u;
-            S.Mk[tid] = 0u;
-            S.done[tid] = 1;
-        } else {
-            S.P[tid] = 0u;
-            S.Mk[tid] = 0u;
-            S.done[tid] = 0;
-        }
-    }
-    if (tid == 0) S.active = (f > 0 && s > 0 && s < n) ? 1 : 0;
-    if (resident) cta_stage<F>(S, side, f, lo, 0, n);
-    __syncthreads();
-
-    // ---- Radix select of the s-th largest key, 8 bits per pass, per column.
-    for (int pass = 0; pass < 4; ++pass) {
-        if (!S.active) break;
-        const int shift = 24 - 8 * pass;
-        const uint32_t hm = pass == 0 ? 0u : (0xffffffffu << (32 - 8 * pass));
-        for (int e = tid; e < F * 256; e += kCtaThreads) (&S.u.hist[0][0])[e] = 0u;
-        __syncthreads();
-        const bool mine = !S.done[a_t];
-        const uint32_t Pa = S.P[a_t];
-        for (int c0 = 0; c0 < n; c0 += kCtaResident) {
-            const int cn = min(kCtaResident, n - c0);
-            if (!resident) cta_stage<F>(S, side, f, lo, c0, cn);
-            if (mine) {
-                for (int k = k0; k < cn; k += kstep) {
-                    const uint32_t key = mag_key(S.x[k][a_t]);
-                    if ((key & hm) == Pa) atomicAdd(&S.u.hist[a_t][(key >> shift) & 255u], 1u);
-                }
-            }
-            if (!resident) __syncthreads();
-        }
-        __syncthreads();
-        // Scan: one warp per column, bins from the top.
-        for (int a = warp; a < F; a += kCtaWarps) {
-            if (S.done[a]) continue;
-            uint32_t c[8];
-            uint32_t lsum = 0;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                c[q] = S.u.hist[a][lane * 8 + q];
-                lsum += c[q];
-            }
-            uint32_t incl = lsum;  // sum over lanes >= this lane
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t t = __shfl_down_sync(kFull, incl, o);
-                if (lane + o < 32) incl += t;
-            }
-            const uint32_t above = incl - lsum;
-            const uint32_t nd = (uint32_t)S.need[a];
-            const bool owner = above < nd && nd <= incl;
-            const unsigned ob = __ballot_sync(kFull, owner);
-            const int L = __ffs(ob) - 1;
-            int digit = 0;
-            uint32_t newneed = 0, inbin = 0;
-            if (lane == L) {
-                uint32_t cum = above;
-#pragma unroll
-                for (int q = 7; q >= 0; --q) {
-                    if (cum + c[q] >= nd && inbin == 0) {
-                        digit = lane * 8 + q;
-                        newneed = nd - cum;
-                        inbin = c[q];
-                    }
-                    if (inbin == 0) cum += c[q];
-                }
-            }
-            digit = __shfl_sync(kFull, digit, L);
-            newneed = __shfl_sync(kFull, newneed, L);
-            inbin = __shfl_sync(kFull, inbin, L);
-            if (lane == 0) {
-                S.P[a] |= (uint32_t)digit << shift;
-                S.Mk[a] = hm | (0xffu << shift);
-                S.need[a] = (int)newneed;
-                if (inbin == newneed) S.done[a] = 1;  // the whole class is kept
-            }
-        }
-        __syncthreads();
-        if (tid == 0) {
-            int act = 0;
-            for (int a = 0; a < F; ++a) act |= !S.done[a];
-            S.active = act;
-        }
-        __syncthreads();
-    }
-    // Columns still open have the full threshold key P and more equal keys
-    // than places: keep the lowest positions (cut = one past the last kept).
-    for (int a = warp; a < F; a += kCtaWarps) {
-        if (S.done[a]) continue;
-        const uint32_t T = S.P[a];
-        const int nd = S.need[a];
-        int seen = 0, cut = n;
-        for (int kb = 0; kb < n; kb += 32) {
-            const int k = kb + lane;
-            bool eq = false;
-            if (k < n) {
-                const float xv = resident ? S.x[k][a]
-                                          : __ldg(side.Y + (int64_t)side.indices[lo + k] * f + a);
-                eq = mag_key(xv) == T;
-            }
-            unsigned b = __ballot_sync(kFull, eq);
-            const int c = __popc(b);
-            if (seen + c >= nd) {
-                int want = nd - seen;
-                while (--want > 0) b &= b - 1u;
-                cut = kb + __ffs(b);  // position of the last kept one, plus one
-                break;
-            }
-            seen += c;
-        }
-        if (lane == 0) S.cut[a] = cut;
-    }
-    __syncthreads();
-
-    // ---- Masked Gram over the row, warps split the positions.
-    constexpr int TA = F / 8, TB = F / 4;
-    const int ta = lane >> 2, tb = lane & 3;
-    const int a0 = ta * TA, b0 = tb * TB;
-    const bool sym = (p.gram_mode == GRAM_SYM);
-    float acc[TA][TB];
-    float rh[TA];
-#pragma unroll
-    for (int q = 0; q < TA; ++q) {
-        rh[q] = 0.f;
-#pragma unroll
-        for (int t = 0; t < TB; ++t) acc[q][t] = 0.f;
-    }
-    const uint32_t Pa = S.P[a_t], Ma = S.Mk[a_t];
-    const int cuta = S.cut[a_t];
-    const uint32_t fmask = (F == 32) ? kFull : ((1u << F) - 1u);
-    for (int c0 = 0; c0 < n; c0 += kCtaResident) {
-        const int cn = min(kCtaResident, n - c0);
-        if (!resident) cta_stage<F>(S, side, f, lo, c0, cn);
-        // Keep masks of this chunk: thread (k, a_t) decides, a ballot packs.
-        for (int kk = 0; kk < cn; kk += kstep) {
-            const int k = kk + k0;
-            bool keep = false;
-            if (k < cn) {
-                const uint32_t key = mag_key(S.x[k][a_t]) & Ma;
-                keep = key > Pa || (key == Pa && (c0 + k) < cuta);
-            }
-            const unsigned b = __ballot_sync(kFull, keep);
-            if (a_t == 0 && k < cn) S.mask[k] = (b >> (lane & ~(F - 1))) & fmask;
-        }
-        __syncthreads();
-        if (masks_out != nullptr) {
-            for (int k = tid; k < cn; k += kCtaThreads) masks_out[lo + c0 + k] = S.mask[k] & ((f == 32) ? kFull : ((1u << f) - 1u));
-        }
-        if (mode != 2) {
-            for (int k = warp; k < cn; k += kCtaWarps) {
-                const uint32_t m = S.mask[k];
-                float xa[TA], xb[TB];
-#pragma unroll
-                for (int q = 0; q < TA; ++q) xa[q] = ((m >> (a0 + q)) & 1u) ? S.x[k][a0 + q] : 0.f;
-#pragma unroll
-                for (int t = 0; t < TB; ++t)
-                    xb[t] = (!sym || ((m >> (b0 + t)) & 1u)) ? S.x[k][b0 + t] : 0.f;
-                const float rk = S.r[k];
-#pragma unroll
-                for (int q = 0; q < TA; ++q) {
-                    rh[q] = fmaf(xa[q], rk, rh[q]);
-#pragma unroll
-                    for (int t = 0; t < TB; ++t) acc[q][t] = fmaf(xa[q], xb[t], acc[q][t]);
-                }
-            }
-        }
-        __syncthreads();
-    }
-    if (mode == 2) return;
-    // Per-warp partials, then a fixed-order reduction over warps.
-#pragma unroll
-    for (int q = 0; q < TA; ++q) {
-#pragma unroll
-        for (int t = 0; t < TB; ++t) S.u.Gp[warp][a0 + q][b0 + t] = acc[q][t];
-        if (tb == 0) S.u.Gp[warp][a0 + q][F] = rh[q];
-    }
-    __syncthreads();
-    float* dst = G_aug + (int64_t)w * F * (F + 1);
-    const float reg = row_reg(n, p);
-    for (int e = tid; e < F * (F + 1); e += kCtaThreads) {
-        const int a = e / (F + 1), b = e % (F + 1);
-        float v = 0.f;
-#pragma unroll
-        for (int q = 0; q < kCtaWarps; ++q) v += S.u.Gp[q][a][b];
-        if (a == b) v = (a < f) ? v + reg : 1.f;
-        dst[e] = v;
-    }
-}
+namespace als {
 
 // ---------------------------------------------------------------------------
 // Batched solve of augmented systems [G | b] (F x (F+1) each, padded rows are

@@ -85,8 +85,37 @@ def test_item_half_sweep_small(core, small):
 
 def test_plain_regulariser_and_min_keep(core, small):
     M0 = synth.init_factor(small.n_m, small.f, 1001)
-    check_half(core, small.train_rows, M0, small.f, 0.1, 0.25, reg="plain")
+    check_half(core, small.train_rows, M0, small.f, 1.0, 0.25, reg="plain")
     check_half(core, small.train_rows, M0, small.f, 0.1, 0.1, min_keep=3)
+
+
+def test_ill_conditioned_rows_meet_fp32_perturbation_bound(core, small):
+    """Plain lambda = 0.1 with r = 0.25 leaves rows whose system has
+    condition number ~5e4: storing that system in FP32 alone moves the
+    solution by ~kappa * 2^-24. Each row must stay within the first-order
+    perturbation bound kappa(G) (|dG|/|G| + |db|/|b|) with both relative
+    perturbations taken as (n_i + n_f) * 2^-24 (FP32 accumulation of n_i
+    products and the elimination)."""
+    M0 = synth.init_factor(small.n_m, small.f, 1001)
+    csr = small.train_rows
+    lam, r = 0.1, 0.25
+    X, _, masks, _ = gpu_half(core, csr, M0, small.f, lam, r, reg="plain")
+    Xo, _, _ = oracle_half(csr, M0, lam, r, reg="plain")
+    G, b = oracle.assemble_half(csr.indptr, csr.indices, csr.values, M0.astype(np.float64), f32(lam), r,
+                                oracle.GRAM_ASYM, oracle.REG_PLAIN)
+    u = 2.0 ** -24
+    L = np.diff(csr.indptr)
+    worst = 0.0
+    for i in range(csr.n_rows):
+        nx = np.linalg.norm(Xo[i])
+        if nx == 0:
+            continue
+        kappa = np.linalg.cond(G[i])
+        bound = kappa * 2 * (L[i] + small.f) * u
+        err = np.linalg.norm(X[i] - Xo[i]) / nx
+        worst = max(worst, err / bound)
+        assert err <= bound, (i, err, bound, kappa)
+    assert worst > 0
 
 
 # ------------------------------------------------------------------ ragged

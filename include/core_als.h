@@ -155,6 +155,36 @@ int als_eval_sse(als_handle* h, int64_t n, const int32_t* iu, const int32_t* im,
 int als_eval_sse_async(als_handle* h, int64_t n, const int32_t* iu, const int32_t* im, const float* r,
                        const float* U, const float* M, double* sse_dev);
 
+/* Test-set SSE that allocates nothing: no handle, no cudaMalloc or cudaFree,
+ * no allocating library call. The paper has no counterpart; this is for
+ * callers that may not allocate device memory when they evaluate:
+ *   - code running while its stream is captured into a CUDA graph, where
+ *     allocation calls are not allowed;
+ *   - programs that give all device memory to their own pool allocator at
+ *     start-up and forbid raw allocations afterwards;
+ *   - services held to a fixed device-memory budget.
+ * Arguments as in als_eval_sse, plus n_f and the stream (a cudaStream_t,
+ * NULL = legacy default stream). The FP64 sum is written to sse_dev without
+ * synchronising.
+ *
+ * Scratch: a file-scope device array of ALS_SSE_STATIC_MAX_BLOCKS FP64
+ * partial sums (32 KiB). Every GPU that loads the library holds it until the
+ * process exits. Each 256-thread block covers up to
+ * ALS_SSE_STATIC_ENTRIES_PER_BLOCK entries, so n may not exceed
+ * ALS_SSE_STATIC_MAX_ENTRIES (2^26): larger n returns ALS_ERR_ARG and
+ * enqueues nothing.
+ * The first call on a device looks up the array's device address with that
+ * device current. Make this first call before any stream capture.
+ * All calls share the one array. A call writes every partial it later reads,
+ * so nothing carries over from a previous call. Calls that overlap on the GPU
+ * (other streams or threads) race on the array and must be serialised by the
+ * caller. */
+#define ALS_SSE_STATIC_MAX_BLOCKS 4096
+#define ALS_SSE_STATIC_ENTRIES_PER_BLOCK 16384
+#define ALS_SSE_STATIC_MAX_ENTRIES ((int64_t)ALS_SSE_STATIC_MAX_BLOCKS * ALS_SSE_STATIC_ENTRIES_PER_BLOCK)
+int als_eval_sse_static(int64_t n, const int32_t* iu, const int32_t* im, const float* r, const float* U,
+                        const float* M, int n_f, double* sse_dev, void* cuda_stream);
+
 /* Kernel timing: while enabled, every kernel the handle launches is
  * bracketed by CUDA events on the handle's stream. als_kernel_time
  * synchronises and returns the summed event time (ms) and the number of

@@ -22,6 +22,7 @@ ALS_REG_WEIGHTED, ALS_REG_PLAIN = 0, 1
 ALS_GRAM_ASYM, ALS_GRAM_SYM, ALS_GRAM_FULL = 0, 1, 2
 ALS_FP32, ALS_TF32, ALS_BF16 = 0, 1, 2
 ALS_FLAG_RATIO, ALS_FLAG_SINGULAR = 1, 2
+ALS_SSE_STATIC_MAX_ENTRIES = 4096 * 16384
 
 
 class AlsError(RuntimeError):
@@ -62,6 +63,7 @@ SIGNATURES = {
     "als_solve": (C.c_int, [_P, _I64, _P, _P, _P, _P]),
     "als_eval_sse": (C.c_int, [_P, _I64, _P, _P, _P, _P, _P, _P]),
     "als_eval_sse_async": (C.c_int, [_P, _I64, _P, _P, _P, _P, _P, _P]),
+    "als_eval_sse_static": (C.c_int, [_I64, _P, _P, _P, _P, _P, C.c_int, _P, _P]),
     "als_profile": (C.c_int, [_P, C.c_int]),
     "als_kernel_time": (C.c_int, [_P, C.c_char_p, _P, _P]),
     "als_get_report": (C.c_int, [_P, _P]),

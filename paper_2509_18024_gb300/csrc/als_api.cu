@@ -774,4 +774,58 @@ const char* als_status_string(int s) {
 
 const char* als_last_error(const als_handle* h) { return h ? h->last_error.c_str() : "null handle"; }
 
+
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free test SSE (als_eval_sse_static). Its FP64 block partials
+// live in this file-scope device array instead of a handle's workspace.
+#include <mutex>
+
+namespace {
+
+static __device__ __align__(256) double g_sse_static_partials[ALS_SSE_STATIC_MAX_BLOCKS];
+
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_sse_static_mu;
+double* g_sse_static_addr[kStaticMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (cudaGetSymbolAddress with that device current).
+int sse_static_scratch(double** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return ALS_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= kStaticMaxDevices) return ALS_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_sse_static_mu);
+    if (g_sse_static_addr[dev] == nullptr) {
+        void* ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_sse_static_partials) != cudaSuccess || ptr == nullptr) {
+            cudaGetLastError();
+            return ALS_ERR_CUDA;
+        }
+        g_sse_static_addr[dev] = static_cast<double*>(ptr);
+    }
+    *out = g_sse_static_addr[dev];
+    return ALS_OK;
+}
+
+}  // namespace
+
+extern "C" int als_eval_sse_static(int64_t n, const int32_t* iu, const int32_t* im, const float* r, const float* U,
+                                   const float* M, int n_f, double* sse_dev, void* cuda_stream) {
+    if (!sse_dev || n < 0 || n_f < 1) return ALS_ERR_ARG;
+    if (n > ALS_SSE_STATIC_MAX_ENTRIES) return ALS_ERR_ARG;  // beyond the static scratch
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    if (n == 0) return cudaMemsetAsync(sse_dev, 0, sizeof(double), st) == cudaSuccess ? ALS_OK : ALS_ERR_CUDA;
+    if (!iu || !im || !r || !U || !M) return ALS_ERR_ARG;
+    double* partials = nullptr;
+    int rc = sse_static_scratch(&partials);
+    if (rc) return rc;
+    const int blocks = (int)((n + ALS_SSE_STATIC_ENTRIES_PER_BLOCK - 1) / ALS_SSE_STATIC_ENTRIES_PER_BLOCK);
+    als::k_sse<<<blocks, als::kEvalThreads, 0, st>>>(n, iu, im, r, U, M, n_f, partials);
+    als::k_sum_partials<<<1, 32, 0, st>>>(partials, blocks, sse_dev);
+    return cudaGetLastError() == cudaSuccess ? ALS_OK : ALS_ERR_CUDA;
+}

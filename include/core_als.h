@@ -51,7 +51,7 @@ extern "C" {
 #define ALS_ERR_TIMEOUT (-5)        /* a bounded device wait ran out */
 #define ALS_ERR_OOM (-6)            /* device allocation failed or workspace cap hit */
 #define ALS_ERR_DEVICE_BOUNDS (-7)  /* a device-side bounds check fired */
-#define ALS_ERR_UNSUPPORTED (-8)    /* option combination not built (e.g. n_f > 32 on FP32) */
+#define ALS_ERR_UNSUPPORTED (-8)    /* option combination not built (e.g. n_f > 128) */
 
 /* Regulariser: weighted lambda n_i (Eq. object function) or plain lambda. */
 #define ALS_REG_WEIGHTED 0
@@ -64,10 +64,19 @@ extern "C" {
 #define ALS_GRAM_SYM 1
 #define ALS_GRAM_FULL 2
 
-/* Arithmetic of the Gram assembly. */
+/* Arithmetic of the Gram assembly (the solve is FP32 in every mode):
+ *   ALS_FP32    FP32 on CUDA cores for n_f <= 32; for n_f > 32 the
+ *               FP32-accurate split TF32 on tensor cores (as ALS_FP32_TC).
+ *   ALS_TF32    TF32 inputs, FP32 accumulation, tensor cores (tcgen05).
+ *   ALS_BF16    BF16 inputs, FP32 accumulation, tensor cores (tcgen05).
+ *   ALS_FP32_TC split TF32 (x = hi + lo, hi*hi + hi*lo + lo*hi accumulated in
+ *               FP32) on tensor cores for every n_f.
+ * Rows with at most 32 observations and n_f <= 32 are assembled in FP32 on
+ * CUDA cores in every mode. */
 #define ALS_FP32 0
 #define ALS_TF32 1
 #define ALS_BF16 2
+#define ALS_FP32_TC 3
 
 /* Per-row flags written by the solve. */
 #define ALS_FLAG_RATIO 1     /* pivot ratio above pivot_ratio_max */
@@ -83,13 +92,13 @@ typedef struct als_csr {
 } als_csr;
 
 typedef struct als_options {
-    int n_f;                 /* rank; 1..32 in this build */
+    int n_f;                 /* rank; 1..128 */
     float lambda;            /* regularisation */
     double budget;           /* CES rate r in [0, 1]; s_i = floor(n_i * r) per column */
     int64_t min_keep;        /* 0 = off; else s_i = min(n_i, max(s_i, min_keep)) */
     int reg_mode;            /* ALS_REG_* */
     int gram_mode;           /* ALS_GRAM_* */
-    int precision;           /* ALS_FP32 (others: ALS_ERR_UNSUPPORTED in this build) */
+    int precision;           /* ALS_FP32, ALS_TF32, ALS_BF16, ALS_FP32_TC */
     double pivot_ratio_max;  /* flag threshold on max pivot / min pivot, e.g. 1e6 */
 } als_options;
 

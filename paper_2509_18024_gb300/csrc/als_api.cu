@@ -19,11 +19,19 @@ using als::Counters;
 using als::Params;
 using als::Side;
 
-// Row plan of one side: rows bucketed by length - warp rows (n_i <= 32),
-// three CTA-resident capacities (<= 128, <= 512, <= 1024) and split rows
-// (> 1024, cut into 512-position chunks); each CTA bucket sorted by length
-// descending so the longest start first.
-constexpr int kBucketCap[3] = {128, 512, 1024};
+// Row plan of one side: rows bucketed by length - warp rows (n_i <= 32, for
+// widths up to 32), three CTA-resident capacities and split rows (longer than
+// the largest capacity, cut into Gram chunks); each bucket sorted by length
+// descending so the longest start first. Capacities by padded width F keep
+// the staged slice plus histograms within shared memory.
+struct BucketCaps {
+    int cap[3];
+};
+BucketCaps bucket_caps(int F) {
+    if (F <= 32) return {{128, 512, 1024}};
+    if (F == 64) return {{128, 256, 512}};
+    return {{32, 64, 128}};
+}
 
 struct Plan {
     const int64_t* indptr = nullptr;
@@ -31,9 +39,10 @@ struct Plan {
     int F = 0;
     int n_warp = 0;
     int n_bucket[3] = {0, 0, 0};
-    int n_slots = 0, n_chunks = 0;
+    int n_slots = 0, n_chunks = 0, n_super = 0;
     int64_t max_len = 0;
-    int32_t* d_lists = nullptr;  // [warp | bucket0 | bucket1 | bucket2 | split rows | c_begin | ch_slot | ch_start]
+    int32_t* d_lists = nullptr;  // [warp | bucket0 | bucket1 | bucket2 | split rows | c_begin | ch_slot | ch_start
+                                 //  | sc_slot | sc_start]
     void* d_split = nullptr;     // split-row selection state and scratch
     int off_bucket(int b) const {
         int o = n_warp;
@@ -179,11 +188,26 @@ int ensure(als_handle* h, DevBuf& b, size_t bytes) {
     return ALS_OK;
 }
 
-int padded_width(int f) {
-    if (f <= 8) return 8;
-    if (f <= 16) return 16;
-    if (f <= 32) return 32;
-    return 0;
+// Padded width: 8, 16, 32 for the CUDA-core engine; 32, 64, 128 for the
+// tensor-core engines (their tiles start at 32 features).
+int padded_width(int f, int precision) {
+    const int lo = (precision == ALS_FP32 && f <= 32) ? 8 : 32;
+    int F = lo;
+    while (F < f) F *= 2;
+    return F <= 128 ? F : 0;
+}
+
+// Gram engine for an option set: FP32 runs on CUDA cores up to 32 features
+// and as split TF32 on tensor cores above; the other precisions always use
+// tensor cores.
+int engine_of(int precision, int F) {
+    switch (precision) {
+        case ALS_FP32: return F <= 32 ? als::ENG_CUDA : als::ENG_TF32X3;
+        case ALS_TF32: return als::ENG_TF32;
+        case ALS_BF16: return als::ENG_BF16;
+        case ALS_FP32_TC: return als::ENG_TF32X3;
+        default: return -1;
+    }
 }
 
 Params make_params(const als_options& o) {
@@ -201,12 +225,12 @@ Params make_params(const als_options& o) {
 int check_options(als_handle* h, const als_options* o) {
     if (!o) return set_err(h, ALS_ERR_ARG, "options are null");
     if (o->n_f < 1) return set_err(h, ALS_ERR_ARG, "n_f must be >= 1");
-    if (o->n_f > 32) return set_err(h, ALS_ERR_UNSUPPORTED, "n_f > 32 is not built in this library");
+    if (o->n_f > 128) return set_err(h, ALS_ERR_UNSUPPORTED, "n_f > 128 is not built in this library");
     if (!(o->budget >= 0.0 && o->budget <= 1.0)) return set_err(h, ALS_ERR_ARG, "budget must be in [0, 1]");
     if (!(o->lambda >= 0.0f) || !std::isfinite(o->lambda)) return set_err(h, ALS_ERR_ARG, "lambda must be >= 0");
     if (o->reg_mode != ALS_REG_WEIGHTED && o->reg_mode != ALS_REG_PLAIN) return set_err(h, ALS_ERR_ARG, "bad reg_mode");
     if (o->gram_mode < ALS_GRAM_ASYM || o->gram_mode > ALS_GRAM_FULL) return set_err(h, ALS_ERR_ARG, "bad gram_mode");
-    if (o->precision != ALS_FP32) return set_err(h, ALS_ERR_UNSUPPORTED, "only ALS_FP32 is built in this library");
+    if (o->precision < ALS_FP32 || o->precision > ALS_FP32_TC) return set_err(h, ALS_ERR_ARG, "bad precision");
     if (o->min_keep < 0) return set_err(h, ALS_ERR_ARG, "min_keep must be >= 0");
     if (!(o->pivot_ratio_max > 0.0)) return set_err(h, ALS_ERR_ARG, "pivot_ratio_max must be > 0");
     return ALS_OK;
@@ -254,27 +278,33 @@ int build_plan(als_handle* h, const als_csr* R, Plan** out) {
     if (err & 2u) return set_err(h, ALS_ERR_CSR, "indices out of range, unsorted or duplicated inside a row");
     if (err & 4u) return set_err(h, ALS_ERR_NONFINITE, "non-finite rating value");
 
-    const int F = padded_width(h->opt.n_f);
+    const int F = padded_width(h->opt.n_f, h->opt.precision);
+    const BucketCaps caps = bucket_caps(F);
+    const int chunk = als::split_chunk(F);
     std::vector<int32_t> warp_rows, bucket[3], split_rows;
     int64_t max_len = 0;
     for (int64_t i = 0; i < R->n_rows; ++i) {
         const int64_t len = indptr[i + 1] - indptr[i];
         max_len = std::max(max_len, len);
-        if (len <= als::kWarpRowMax) warp_rows.push_back((int32_t)i);
-        else if (len <= kBucketCap[0]) bucket[0].push_back((int32_t)i);
-        else if (len <= kBucketCap[1]) bucket[1].push_back((int32_t)i);
-        else if (len <= kBucketCap[2]) bucket[2].push_back((int32_t)i);
+        if (len <= als::kWarpRowMax && F <= 32) warp_rows.push_back((int32_t)i);
+        else if (len <= caps.cap[0]) bucket[0].push_back((int32_t)i);
+        else if (len <= caps.cap[1]) bucket[1].push_back((int32_t)i);
+        else if (len <= caps.cap[2]) bucket[2].push_back((int32_t)i);
         else split_rows.push_back((int32_t)i);
     }
     auto longer = [&](int32_t a, int32_t b) { return indptr[a + 1] - indptr[a] > indptr[b + 1] - indptr[b]; };
     for (auto& v : bucket) std::stable_sort(v.begin(), v.end(), longer);
     std::stable_sort(split_rows.begin(), split_rows.end(), longer);
-    std::vector<int32_t> c_begin(1, 0), ch_slot, ch_start;
+    std::vector<int32_t> c_begin(1, 0), ch_slot, ch_start, sc_slot, sc_start;
     for (size_t q = 0; q < split_rows.size(); ++q) {
         const int64_t len = indptr[split_rows[q] + 1] - indptr[split_rows[q]];
-        for (int64_t st = 0; st < len; st += als::kSplitChunk) {
+        for (int64_t st = 0; st < len; st += chunk) {
             ch_slot.push_back((int32_t)q);
             ch_start.push_back((int32_t)st);
+        }
+        for (int64_t st = 0; st < len; st += als::kSplitSuper) {
+            sc_slot.push_back((int32_t)q);
+            sc_start.push_back((int32_t)st);
         }
         c_begin.push_back((int32_t)ch_slot.size());
     }
@@ -288,6 +318,7 @@ int build_plan(als_handle* h, const als_csr* R, Plan** out) {
     for (int q = 0; q < 3; ++q) p.n_bucket[q] = (int)bucket[q].size();
     p.n_slots = (int)split_rows.size();
     p.n_chunks = (int)ch_slot.size();
+    p.n_super = (int)sc_slot.size();
     p.max_len = max_len;
     std::vector<int32_t> lists(warp_rows);
     for (auto& v : bucket) lists.insert(lists.end(), v.begin(), v.end());
@@ -295,6 +326,8 @@ int build_plan(als_handle* h, const als_csr* R, Plan** out) {
     lists.insert(lists.end(), c_begin.begin(), c_begin.end());
     lists.insert(lists.end(), ch_slot.begin(), ch_slot.end());
     lists.insert(lists.end(), ch_start.begin(), ch_start.end());
+    lists.insert(lists.end(), sc_slot.begin(), sc_slot.end());
+    lists.insert(lists.end(), sc_start.begin(), sc_start.end());
     cudaError_t e = cudaMalloc(&p.d_lists, lists.size() * sizeof(int32_t));
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -321,18 +354,19 @@ int build_plan(als_handle* h, const als_csr* R, Plan** out) {
     return ALS_OK;
 }
 
-template <int F, int NS>
+template <int F, int NS, int ENG>
 int launch_cta_bucket(als_handle* h, const Side& side, const Params& p, const int32_t* list, int count, int mode,
                       float* G_aug, uint32_t* masks_out) {
     if (count == 0) return ALS_OK;
-    const size_t smem = sizeof(als::CtaSmem<F, NS>);
-    ALS_CUDA(h, cudaFuncSetAttribute(als::k_cta_rows<F, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    ALS_LAUNCH(h, "cta_rows", als::k_cta_rows<F, NS><<<count, als::kCtaThreads, smem, h->stream>>>(
+    const size_t smem = sizeof(als::CtaSmem<F, NS, ENG>);
+    ALS_CUDA(h, cudaFuncSetAttribute(als::k_cta_rows<F, NS, ENG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    ALS_LAUNCH(h, "cta_rows", als::k_cta_rows<F, NS, ENG><<<count, als::kCtaThreads, smem, h->stream>>>(
                                   side, p, list, count, mode, G_aug, masks_out));
     return ALS_OK;
 }
 
-template <int F>
+template <int F, int ENG>
 int launch_split(als_handle* h, const Plan& pl, const Side& side, const Params& p, int mode, float* G_aug,
                  uint32_t* masks_out) {
     if (pl.n_slots == 0) return ALS_OK;
@@ -343,8 +377,11 @@ int launch_split(als_handle* h, const Plan& pl, const Side& side, const Params& 
     sp.c_begin = sp.row + pl.n_slots;
     sp.ch_slot = sp.c_begin + pl.n_slots + 1;
     sp.ch_start = sp.ch_slot + pl.n_chunks;
+    sp.sc_slot = sp.ch_start + pl.n_chunks;
+    sp.sc_start = sp.sc_slot + pl.n_super;
     sp.n_slots = pl.n_slots;
     sp.n_chunks = pl.n_chunks;
+    sp.n_super = pl.n_super;
     const SplitLayout L(pl.n_slots, pl.n_chunks, F);
     char* mem = reinterpret_cast<char*>(pl.d_split);
     als::SplitState ss;
@@ -358,23 +395,53 @@ int launch_split(als_handle* h, const Plan& pl, const Side& side, const Params& 
     ss.part = reinterpret_cast<float*>(mem + L.part);
     const int sc = pl.n_slots * F;
     ALS_LAUNCH(h, "split_init", als::k_split_init<F><<<(sc + 255) / 256, 256, 0, st>>>(side, p, sp, ss));
+    const size_t hsmem = (size_t)F * als::kHistRow * 4;
+    ALS_CUDA(h, cudaFuncSetAttribute(als::k_split_hist<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem));
     for (int pass = 0; pass < 4; ++pass) {
-        ALS_LAUNCH(h, "split_hist", als::k_split_hist<F><<<pl.n_chunks, als::kCtaThreads, 0, st>>>(side, p, sp, ss, pass));
+        ALS_LAUNCH(h, "split_hist",
+                   als::k_split_hist<F><<<pl.n_super, als::kCtaThreads, hsmem, st>>>(side, p, sp, ss, pass));
         ALS_LAUNCH(h, "split_scan", als::k_split_scan<F><<<(sc * 32 + 255) / 256, 256, 0, st>>>(sp, ss, pass));
     }
     ALS_LAUNCH(h, "split_eqcount", als::k_split_eqcount<F><<<pl.n_chunks, als::kCtaThreads, 0, st>>>(side, p, sp, ss));
     ALS_LAUNCH(h, "split_cut", als::k_split_cut<F><<<(sc * 32 + 255) / 256, 256, 0, st>>>(side, p, sp, ss));
-    const size_t smem = sizeof(als::SplitGramSmem<F>);
-    ALS_CUDA(h, cudaFuncSetAttribute(als::k_split_gram<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    ALS_LAUNCH(h, "split_gram", als::k_split_gram<F><<<pl.n_chunks, als::kCtaThreads, smem, st>>>(side, p, sp, ss, mode,
-                                                                                                 masks_out));
+    const size_t smem = sizeof(als::SplitGramSmem<F, ENG>);
+    ALS_CUDA(h, cudaFuncSetAttribute(als::k_split_gram<F, ENG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    ALS_LAUNCH(h, "split_gram", als::k_split_gram<F, ENG><<<pl.n_chunks, als::kCtaThreads, smem, st>>>(
+                                    side, p, sp, ss, mode, masks_out));
     if (mode != 2)
-        ALS_LAUNCH(h, "split_reduce", als::k_split_reduce<F><<<pl.n_slots, als::kCtaThreads, 0, st>>>(side, p, sp, ss, G_aug));
+        ALS_LAUNCH(h, "split_reduce",
+                   als::k_split_reduce<F><<<pl.n_slots, als::kCtaThreads, 0, st>>>(side, p, sp, ss, G_aug));
     return ALS_OK;
 }
 
-// mode 0: solve into X_out; 1: assembled systems into G_out/b_out; 2: masks only.
+// Batched solve of augmented systems listed by `list` (null: identity).
 template <int F>
+int launch_solve(als_handle* h, const float* aug, const int32_t* list, int count, const Params& p, float* X_out,
+                 int32_t* flags_out) {
+    if (count == 0) return ALS_OK;
+    if constexpr (F <= 32) {
+        ALS_LAUNCH(h, "solve_rows", als::k_solve_rows<F><<<(count + 7) / 8, 256, 0, h->stream>>>(
+                                        aug, list, count, p, X_out, flags_out, counters(h)));
+    } else {
+        const size_t smem = (size_t)F * (F + 1) * sizeof(float);
+        ALS_CUDA(h, cudaFuncSetAttribute(als::k_solve_big<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        ALS_LAUNCH(h, "solve_rows", als::k_solve_big<F><<<count, als::kBigSolveThreads, smem, h->stream>>>(
+                                        aug, list, count, p, X_out, flags_out, counters(h)));
+    }
+    return ALS_OK;
+}
+
+// Bucket capacities as template arguments.
+template <int F>
+struct Caps {
+    static constexpr int c0 = F <= 32 ? 128 : (F == 64 ? 128 : 32);
+    static constexpr int c1 = F <= 32 ? 512 : (F == 64 ? 256 : 64);
+    static constexpr int c2 = F <= 32 ? 1024 : (F == 64 ? 512 : 128);
+};
+
+// mode 0: solve into X_out; 1: assembled systems into G_out/b_out; 2: masks only.
+template <int F, int ENG>
 int run_side(als_handle* h, const Plan& pl, const Side& side, int mode, float* X_out, int32_t* flags_out,
              uint32_t* masks_out, float* G_out, float* b_out) {
     cudaStream_t st = h->stream;
@@ -388,18 +455,18 @@ int run_side(als_handle* h, const Plan& pl, const Side& side, int mode, float* X
     float* aug_b0 = aug_split + (size_t)pl.n_slots * F * (F + 1);
     float* aug_b1 = aug_b0 + (size_t)pl.n_bucket[0] * F * (F + 1);
     float* aug_b2 = aug_b1 + (size_t)pl.n_bucket[1] * F * (F + 1);
-    rc = launch_split<F>(h, pl, side, p, mode, aug_split, masks_out);
+    rc = launch_split<F, ENG>(h, pl, side, p, mode, aug_split, masks_out);
     if (rc) return rc;
     const int32_t* lists = pl.d_lists;
-    rc = launch_cta_bucket<F, 1024>(h, side, p, lists + pl.off_bucket(2), pl.n_bucket[2], mode, aug_b2, masks_out);
+    rc = launch_cta_bucket<F, Caps<F>::c2, ENG>(h, side, p, lists + pl.off_bucket(2), pl.n_bucket[2], mode, aug_b2,
+                                               masks_out);
     if (rc) return rc;
-    rc = launch_cta_bucket<F, 512>(h, side, p, lists + pl.off_bucket(1), pl.n_bucket[1], mode, aug_b1, masks_out);
+    rc = launch_cta_bucket<F, Caps<F>::c1, ENG>(h, side, p, lists + pl.off_bucket(1), pl.n_bucket[1], mode, aug_b1,
+                                               masks_out);
     if (rc) return rc;
-    rc = launch_cta_bucket<F, 128>(h, side, p, lists + pl.off_bucket(0), pl.n_bucket[0], mode, aug_b0, masks_out);
+    rc = launch_cta_bucket<F, Caps<F>::c0, ENG>(h, side, p, lists + pl.off_bucket(0), pl.n_bucket[0], mode, aug_b0,
+                                               masks_out);
     if (rc) return rc;
-    // Systems of the split and CTA rows, in G_aug order: split rows first,
-    // then buckets 0..2 (the lists are laid out in the same order apart from
-    // the split rows, which follow the buckets in the list array).
     struct Seg { const int32_t* list; int count; float* aug; };
     const Seg segs[4] = {{lists + pl.off_split(), pl.n_slots, aug_split},
                          {lists + pl.off_bucket(0), pl.n_bucket[0], aug_b0},
@@ -408,22 +475,47 @@ int run_side(als_handle* h, const Plan& pl, const Side& side, int mode, float* X
     for (const Seg& sg : segs) {
         if (sg.count == 0) continue;
         if (mode == 0) {
-            ALS_LAUNCH(h, "solve_rows", als::k_solve_rows<F><<<(sg.count + 7) / 8, 256, 0, st>>>(
-                                            sg.aug, sg.list, sg.count, p, X_out, flags_out, counters(h)));
+            rc = launch_solve<F>(h, sg.aug, sg.list, sg.count, p, X_out, flags_out);
+            if (rc) return rc;
         } else if (mode == 1) {
             ALS_LAUNCH(h, "unpack_aug", als::k_unpack_aug<F><<<1024, 256, 0, st>>>(sg.aug, sg.list, sg.count, p.f,
                                                                                     G_out, b_out));
         }
     }
-    if (pl.n_warp > 0) {
-        ALS_LAUNCH(h, "warp_rows", als::k_warp_rows<F><<<(pl.n_warp + 7) / 8, 256, 0, st>>>(
-                                       side, p, lists, pl.n_warp, mode, X_out, flags_out, masks_out, G_aug,
-                                       counters(h)));
-        if (mode == 1)
-            ALS_LAUNCH(h, "unpack_aug", als::k_unpack_aug<F><<<1024, 256, 0, st>>>(G_aug, lists, pl.n_warp, p.f,
-                                                                                    G_out, b_out));
+    if constexpr (F <= 32) {
+        if (pl.n_warp > 0) {
+            ALS_LAUNCH(h, "warp_rows", als::k_warp_rows<F><<<(pl.n_warp + 7) / 8, 256, 0, st>>>(
+                                           side, p, lists, pl.n_warp, mode, X_out, flags_out, masks_out, G_aug,
+                                           counters(h)));
+            if (mode == 1)
+                ALS_LAUNCH(h, "unpack_aug", als::k_unpack_aug<F><<<1024, 256, 0, st>>>(G_aug, lists, pl.n_warp, p.f,
+                                                                                        G_out, b_out));
+        }
     }
     return ALS_OK;
+}
+
+// All built (width, engine) pairs.
+int run_side_any(als_handle* h, const Plan& pl, const Side& side, int mode, float* X_out, int32_t* flags_out,
+                 uint32_t* masks_out, float* G_out, float* b_out) {
+    const int F = padded_width(h->opt.n_f, h->opt.precision);
+    const int eng = engine_of(h->opt.precision, F);
+#define ALS_RUN(FF, EE)                                                                          \
+    if (F == FF && eng == EE) return run_side<FF, EE>(h, pl, side, mode, X_out, flags_out, masks_out, G_out, b_out)
+    ALS_RUN(8, als::ENG_CUDA);
+    ALS_RUN(16, als::ENG_CUDA);
+    ALS_RUN(32, als::ENG_CUDA);
+    ALS_RUN(32, als::ENG_BF16);
+    ALS_RUN(32, als::ENG_TF32);
+    ALS_RUN(32, als::ENG_TF32X3);
+    ALS_RUN(64, als::ENG_BF16);
+    ALS_RUN(64, als::ENG_TF32);
+    ALS_RUN(64, als::ENG_TF32X3);
+    ALS_RUN(128, als::ENG_BF16);
+    ALS_RUN(128, als::ENG_TF32);
+    ALS_RUN(128, als::ENG_TF32X3);
+#undef ALS_RUN
+    return set_err(h, ALS_ERR_UNSUPPORTED, "n_f %d with precision %d is not built", h->opt.n_f, h->opt.precision);
 }
 
 int dispatch_side(als_handle* h, const als_csr* R, const float* Y, int mode, float* X_out, int32_t* flags_out,
@@ -442,12 +534,7 @@ int dispatch_side(als_handle* h, const als_csr* R, const float* Y, int mode, flo
     side.n_rows = R->n_rows;
     side.n_cols = R->n_cols;
     if (mode == 0) ALS_CUDA(h, cudaMemsetAsync(counters(h), 0, sizeof(Counters), h->stream));
-    switch (padded_width(h->opt.n_f)) {
-        case 8: return run_side<8>(h, *pl, side, mode, X_out, flags_out, masks_out, G_out, b_out);
-        case 16: return run_side<16>(h, *pl, side, mode, X_out, flags_out, masks_out, G_out, b_out);
-        case 32: return run_side<32>(h, *pl, side, mode, X_out, flags_out, masks_out, G_out, b_out);
-        default: return set_err(h, ALS_ERR_UNSUPPORTED, "n_f not supported");
-    }
+    return run_side_any(h, *pl, side, mode, X_out, flags_out, masks_out, G_out, b_out);
 }
 
 template <int F>
@@ -459,9 +546,7 @@ int solve_systems(als_handle* h, int64_t n_rows, const float* G, const float* b,
     float* G_aug = reinterpret_cast<float*>(h->g_aug.p);
     ALS_CUDA(h, cudaMemsetAsync(counters(h), 0, sizeof(Counters), st));
     ALS_LAUNCH(h, "pack_aug", als::k_pack_aug<F><<<1024, 256, 0, st>>>(G, b, n_rows, p.f, G_aug));
-    ALS_LAUNCH(h, "solve_rows", als::k_solve_rows<F><<<(int)((n_rows + 7) / 8), 256, 0, st>>>(G_aug, nullptr, (int)n_rows, p, X_out, flags_out,
-                                                                  counters(h)));
-    return ALS_OK;
+    return launch_solve<F>(h, G_aug, nullptr, (int)n_rows, p, X_out, flags_out);
 }
 
 }  // namespace
@@ -567,10 +652,12 @@ int als_solve(als_handle* h, int64_t n_rows, const float* G, const float* b, flo
     if (n_rows < 0 || n_rows > 0x7fffffff) return set_err(h, ALS_ERR_ARG, "bad n_rows");
     if (n_rows == 0) return ALS_OK;
     if (!G || !b || !X_out) return set_err(h, ALS_ERR_ARG, "null buffer");
-    switch (padded_width(h->opt.n_f)) {
+    switch (padded_width(h->opt.n_f, h->opt.precision)) {
         case 8: return solve_systems<8>(h, n_rows, G, b, X_out, flags_out);
         case 16: return solve_systems<16>(h, n_rows, G, b, X_out, flags_out);
         case 32: return solve_systems<32>(h, n_rows, G, b, X_out, flags_out);
+        case 64: return solve_systems<64>(h, n_rows, G, b, X_out, flags_out);
+        case 128: return solve_systems<128>(h, n_rows, G, b, X_out, flags_out);
         default: return set_err(h, ALS_ERR_UNSUPPORTED, "n_f not supported");
     }
 }
@@ -751,7 +838,8 @@ int64_t als_workspace_bytes(const als_handle* h) {
     if (!h) return 0;
     int64_t b = (int64_t)(h->g_aug.bytes + h->misc.bytes + h->host_in.bytes);
     for (const auto& p : h->plans)
-        b += (int64_t)SplitLayout(p.n_slots, p.n_chunks, p.F).total + (int64_t)(p.n_rows + 2 * p.n_chunks + p.n_slots + 1) * 4;
+        b += (int64_t)SplitLayout(p.n_slots, p.n_chunks, p.F).total +
+             (int64_t)(p.n_rows + 2 * p.n_chunks + 2 * p.n_super + p.n_slots + 1) * 4;
     return b;
 }
 

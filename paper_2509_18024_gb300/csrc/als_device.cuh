@@ -230,17 +230,34 @@ struct BinPick {
     uint32_t inbin;    // keys in that bin
 };
 
-// Warp-cooperative scan of 256 bins (any address space) from the top bin
-// down: the bin where the running count first reaches `need` (>= 1; the bins
-// must hold at least `need` keys in total).
-__device__ __forceinline__ BinPick warp_pick_bin(const uint32_t* bins, uint32_t need) {
+// Shared-memory histogram layout: bin b of column a at a * kHistRow + b +
+// b / 32. Lanes working on different columns with the same bin hit banks
+// 9a + ... (distinct, 9 is odd), and a lane reading its 8 consecutive bins
+// 8l..8l+7 hits bank 8l + l/4 + q (distinct over the 32 lanes).
+constexpr int kHistRow = 265;
+__device__ __forceinline__ int hist_slot(int b) { return b + (b >> 5); }
+
+// Warp-cooperative scan of 256 bins from the top bin down: the bin where the
+// running count first reaches `need` (>= 1; the bins must hold at least
+// `need` keys in total). Padded = shared-memory layout above; otherwise the
+// 256 bins are contiguous. With `zero`, the bins are cleared after reading.
+template <bool Padded>
+__device__ __forceinline__ BinPick warp_pick_bin(uint32_t* bins, uint32_t need, bool zero) {
     const int lane = threadIdx.x & 31;
     uint32_t c[8];
     uint32_t lsum = 0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        c[q] = bins[lane * 8 + q];
+        const int b = lane * 8 + q;
+        c[q] = bins[Padded ? hist_slot(b) : b];
         lsum += c[q];
+    }
+    if (zero) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int b = lane * 8 + q;
+            bins[Padded ? hist_slot(b) : b] = 0u;
+        }
     }
     uint32_t incl = lsum;  // keys in bins of lanes >= this lane
 #pragma unroll

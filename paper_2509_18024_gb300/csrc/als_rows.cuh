@@ -3,14 +3,42 @@
 // masked Gram of Eq. (core_ui) in FP32 on CUDA cores.
 #pragma once
 
+#include <type_traits>
+
 #include "als_device.cuh"
+#include "als_tc.cuh"
 
 namespace als {
 
 constexpr int kCtaThreads = 256;
 constexpr int kCtaWarps = kCtaThreads / 32;
-constexpr int kSplitChunk = 512;  // elements per chunk of a split row
-constexpr int kSplitMin = 1024;   // rows longer than this are split
+constexpr int kSplitSuper = 4096;  // positions per histogram block of a split row
+constexpr int kGatherBatch = 8;    // independent gathers in flight per thread
+
+// Gram engines: FP32 on CUDA cores (n_f <= 32), or tcgen05 in BF16, TF32,
+// or split TF32 (FP32-accurate).
+enum { ENG_CUDA = 0, ENG_BF16 = 1, ENG_TF32 = 2, ENG_TF32X3 = 3 };
+__host__ __device__ constexpr int tc_prec(int eng) { return eng == ENG_BF16 ? TC_BF16 : (eng == ENG_TF32 ? TC_TF32 : TC_TF32X3); }
+
+// Positions per Gram chunk of a split row, by padded width.
+template <int F>
+struct SplitChunk {
+    static constexpr int value = F <= 32 ? 512 : (F == 64 ? 256 : 128);
+};
+__host__ __device__ constexpr int split_chunk(int F) { return F <= 32 ? 512 : (F == 64 ? 256 : 128); }
+
+// Mask words per position.
+template <int F>
+struct MaskWords {
+    static constexpr int value = (F + 31) / 32;
+};
+
+// Bytes of the Gram scratch (partials or tensor-core tiles) for an engine.
+template <int F, int ENG>
+struct GramScratch {
+    static constexpr int value =
+        ENG == ENG_CUDA ? kCtaWarps * F * (F + 1) * 4 : TcCfg<F, (ENG == ENG_CUDA ? 0 : tc_prec(ENG))>::TILE_BYTES;
+};
 
 // ---------------------------------------------------------------------------
 // Masked Gram of a staged tile, warps split the positions, lanes tile [G|b]:
@@ -28,7 +56,8 @@ struct GramAcc {
             for (int t = 0; t < TB; ++t) acc[q][t] = 0.f;
         }
     }
-    // x: [*][F] row-major tile, mask: keep bits per position, r: ratings.
+    // x: [*][F] row-major tile, mask: keep bits per position (F <= 32: one
+    // word), r: ratings.
     __device__ __forceinline__ void add_tile(const float (*x)[F], const uint32_t* mask, const float* r, int k_begin,
                                              int k_end, int k_step, bool sym) {
         const int lane = threadIdx.x & 31;
@@ -70,9 +99,20 @@ __device__ __forceinline__ void stage_tile(float (*x)[F], float* r, int32_t* idx
         r[k] = side.values[e0 + k];
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < cn * F; e += kCtaThreads) {
-        const int k = e / F, a = e % F;
-        x[k][a] = (a < f) ? __ldg(side.Y + (int64_t)idx[k] * f + a) : 0.f;
+    const int total = cn * F;
+    for (int e0 = threadIdx.x; e0 < total; e0 += kCtaThreads * kGatherBatch) {
+        float v[kGatherBatch];
+#pragma unroll
+        for (int u = 0; u < kGatherBatch; ++u) {
+            const int e = e0 + u * kCtaThreads;
+            const int k = e / F, a = e % F;
+            v[u] = (e < total && a < f) ? __ldg(side.Y + (int64_t)idx[k] * f + a) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < kGatherBatch; ++u) {
+            const int e = e0 + u * kCtaThreads;
+            if (e < total) x[e / F][e % F] = v[u];
+        }
     }
     __syncthreads();
 }
@@ -97,33 +137,94 @@ __device__ __forceinline__ void init_column(int a, int f, long long s, long long
 }
 
 // ---------------------------------------------------------------------------
+// Keep masks of a staged tile: thread (k, a_t) applies its column's keep
+// rule, a ballot packs the bits. pos0 = position of tile row 0 in its row.
+template <int F>
+__device__ __forceinline__ void build_masks(uint32_t (*mask)[MaskWords<F>::value], const float (*x)[F], int cn,
+                                            int pos0, uint32_t Pa, uint32_t Ma, int cuta) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int a_t = tid % F, k0 = tid / F;
+    constexpr int kstep = kCtaThreads / F;
+    for (int kk = 0; kk < cn; kk += kstep) {
+        const int k = kk + k0;
+        const bool keep = k < cn && keep_rule(mag_key(x[k][a_t]), Pa, Ma, pos0 + k, cuta);
+        const unsigned b = __ballot_sync(kFull, keep);
+        if constexpr (F >= 32) {
+            if (lane == 0 && k < cn) mask[k][a_t >> 5] = b;
+        } else {
+            const uint32_t fmask = (1u << F) - 1u;
+            if (a_t == 0 && k < cn) mask[k][0] = (b >> (lane & ~(F - 1))) & fmask;
+        }
+    }
+}
+
+// Masked Gram of positions [0, cn) of a staged tile. The result (no
+// regulariser) goes to out(a, c, v) for a < F, c <= F, called once per value
+// by some thread. scratch: GramScratch bytes; bar/tmem_slot for tcgen05.
+template <int F, int ENG, class Out>
+__device__ __forceinline__ void gram_tile(uint8_t* scratch, uint64_t* bar, uint32_t* tmem_slot, const float (*x)[F],
+                                          const uint32_t (*mask)[MaskWords<F>::value], const float* r, int cn,
+                                          bool sym, Out out) {
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if constexpr (ENG == ENG_CUDA) {
+        static_assert(F <= 32, "CUDA-core Gram is built for n_f <= 32");
+        float (*Gp)[F][F + 1] = reinterpret_cast<float (*)[F][F + 1]>(scratch);
+        GramAcc<F> g;
+        g.zero();
+        g.add_tile(x, &mask[0][0], r, warp, cn, kCtaWarps, sym);
+        g.store(Gp[warp]);
+        __syncthreads();
+        for (int e = tid; e < F * (F + 1); e += kCtaThreads) {
+            const int a = e / (F + 1), c = e % (F + 1);
+            float v = 0.f;
+#pragma unroll
+            for (int q = 0; q < kCtaWarps; ++q) v += Gp[q][a][c];
+            out(a, c, v);
+        }
+    } else {
+        constexpr int PREC = tc_prec(ENG);
+        TcCtx ctx;
+        tc_setup<F, PREC>(scratch, bar, tmem_slot, ctx);
+        tc_accumulate<F, PREC, MaskWords<F>::value>(ctx, scratch, bar, x, mask, r, 0, cn, sym, true);
+        tc_store<F, PREC>(ctx, cn <= 0, out);
+        tc_teardown<F, PREC>(ctx);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // CTA per row, slice resident in shared memory (n_i <= NS).
-template <int F, int NS>
+template <int F, int NS, int ENG>
 struct CtaSmem {
+    static constexpr int W = MaskWords<F>::value;
+    static constexpr int HIST_BYTES = F * kHistRow * 4;
+    static constexpr int GRAM_BYTES = GramScratch<F, ENG>::value;
+    static constexpr int U_BYTES = HIST_BYTES > GRAM_BYTES ? HIST_BYTES : GRAM_BYTES;
     float x[NS][F];
     float r[NS];
     int32_t idx[NS];
-    uint32_t mask[NS];
-    union {
-        uint32_t hist[F][256];
-        float Gp[kCtaWarps][F][F + 1];
-    } u;
+    uint32_t mask[NS][W];
+    __align__(1024) uint8_t u[U_BYTES];  // histograms, then Gram scratch
+    uint64_t bar;
+    uint32_t tmem_slot;
     uint32_t P[F];
     uint32_t Mk[F];
     int32_t need[F];
     int32_t cut[F];
     int32_t done[F];
-    int32_t active;
+    int32_t open_after[4];  // columns still open after each pass
+    __device__ uint32_t (*hist())[kHistRow] { return reinterpret_cast<uint32_t (*)[kHistRow]>(u); }
 };
 
 // mode 0/1: write the augmented system of list entry w to G_aug[w]; mode 2:
 // masks only.
-template <int F, int NS>
+template <int F, int NS, int ENG>
 __global__ void __launch_bounds__(kCtaThreads) k_cta_rows(Side side, Params p, const int32_t* __restrict__ rows,
                                                           int n_list, int mode, float* __restrict__ G_aug,
                                                           uint32_t* __restrict__ masks_out) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    CtaSmem<F, NS>& S = *reinterpret_cast<CtaSmem<F, NS>*>(smem_raw);
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    using Smem = CtaSmem<F, NS, ENG>;
+    Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+    constexpr int W = Smem::W;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int w = blockIdx.x;
     if (w >= n_list) return;
@@ -135,6 +236,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_cta_rows(Side side, Params p, c
     const int a_t = tid % F;  // thread t always handles column t mod F
     const int k0 = tid / F;
     constexpr int kstep = kCtaThreads / F;
+    uint32_t (*hist)[kHistRow] = S.hist();
 
     if (tid < F) {
         uint32_t P, Mk;
@@ -146,39 +248,35 @@ __global__ void __launch_bounds__(kCtaThreads) k_cta_rows(Side side, Params p, c
         S.cut[tid] = cut;
         S.done[tid] = done;
     }
-    if (tid == 0) S.active = (f > 0 && s > 0 && s < n) ? 1 : 0;
+    if (tid < 4) S.open_after[tid] = 0;
+    // Histograms start at zero; each scan re-zeroes the bins it read.
+    for (int e = tid; e < F * kHistRow; e += kCtaThreads) (&hist[0][0])[e] = 0u;
     stage_tile<F>(S.x, S.r, S.idx, side, f, lo, n);
 
-    for (int pass = 0; pass < 4; ++pass) {
-        if (!S.active) break;
+    bool active = f > 0 && s > 0 && s < n;
+    for (int pass = 0; pass < 4 && active; ++pass) {
         const uint32_t hm = radix_before(pass);
-        for (int e = tid; e < F * 256; e += kCtaThreads) (&S.u.hist[0][0])[e] = 0u;
-        __syncthreads();
         if (!S.done[a_t]) {
             const uint32_t Pa = S.P[a_t];
             for (int k = k0; k < n; k += kstep) {
                 const uint32_t key = mag_key(S.x[k][a_t]);
-                if ((key & hm) == Pa) atomicAdd(&S.u.hist[a_t][radix_digit(key, pass)], 1u);
+                if ((key & hm) == Pa) atomicAdd(&hist[a_t][hist_slot(radix_digit(key, pass))], 1u);
             }
         }
         __syncthreads();
         for (int a = warp; a < F; a += kCtaWarps) {
             if (S.done[a]) continue;
-            const BinPick bp = warp_pick_bin(S.u.hist[a], (uint32_t)S.need[a]);
+            const BinPick bp = warp_pick_bin<true>(hist[a], (uint32_t)S.need[a], true);
             if (lane == 0) {
                 S.P[a] |= (uint32_t)bp.digit << radix_shift(pass);
                 S.Mk[a] = radix_after(pass);
                 S.need[a] = (int)bp.newneed;
                 if (bp.inbin == bp.newneed) S.done[a] = 1;
+                else atomicAdd(&S.open_after[pass], 1);
             }
         }
         __syncthreads();
-        if (tid == 0) {
-            int act = 0;
-            for (int a = 0; a < F; ++a) act |= !S.done[a];
-            S.active = act;
-        }
-        __syncthreads();
+        active = S.open_after[pass] > 0;
     }
     // Open columns: the full key P has more copies than places left; keep the
     // lowest positions.
@@ -203,46 +301,33 @@ __global__ void __launch_bounds__(kCtaThreads) k_cta_rows(Side side, Params p, c
         if (lane == 0) S.cut[a] = cut;
     }
     __syncthreads();
-
-    const uint32_t Pa = S.P[a_t], Ma = S.Mk[a_t];
-    const int cuta = S.cut[a_t];
-    const uint32_t fmask = (F == 32) ? kFull : ((1u << F) - 1u);
-    for (int kk = 0; kk < n; kk += kstep) {
-        const int k = kk + k0;
-        const bool keep = k < n && keep_rule(mag_key(S.x[k][a_t]), Pa, Ma, k, cuta);
-        const unsigned b = __ballot_sync(kFull, keep);
-        if (a_t == 0 && k < n) S.mask[k] = (b >> (lane & ~(F - 1))) & fmask;
-    }
+    build_masks<F>(S.mask, S.x, n, 0, S.P[a_t], S.Mk[a_t], S.cut[a_t]);
     __syncthreads();
     if (masks_out != nullptr)
-        for (int k = tid; k < n; k += kCtaThreads) masks_out[lo + k] = S.mask[k];
+        for (int e = tid; e < n * W; e += kCtaThreads) masks_out[lo * W + e] = (&S.mask[0][0])[e];
     if (mode == 2) return;
-    GramAcc<F> g;
-    g.zero();
-    g.add_tile(S.x, S.mask, S.r, warp, n, kCtaWarps, p.gram_mode == GRAM_SYM);
-    g.store(S.u.Gp[warp]);
-    __syncthreads();
     float* dst = G_aug + (int64_t)w * F * (F + 1);
     const float reg = row_reg(n, p);
-    for (int e = tid; e < F * (F + 1); e += kCtaThreads) {
-        const int a = e / (F + 1), b = e % (F + 1);
-        float v = 0.f;
-#pragma unroll
-        for (int q = 0; q < kCtaWarps; ++q) v += S.u.Gp[q][a][b];
-        if (a == b) v = (a < f) ? v + reg : 1.f;
-        dst[e] = v;
-    }
+    gram_tile<F, ENG>(S.u, &S.bar, &S.tmem_slot, S.x, S.mask, S.r, n, p.gram_mode == GRAM_SYM,
+                      [&](int a, int c, float v) {
+                          if (a == c) v = (a < f) ? v + reg : 1.f;
+                          dst[a * (F + 1) + c] = v;
+                      });
 }
 
 // ---------------------------------------------------------------------------
-// Split rows (n_i > kSplitMin): one CTA per chunk of kSplitChunk positions.
+// Split rows (longer than the largest resident bucket): Gram chunks of
+// SplitChunk<F> positions, histogram blocks of kSplitSuper positions.
 struct SplitPlan {
     const int32_t* row;      // [n_slots] row id of each slot
     const int32_t* c_begin;  // [n_slots + 1] chunk range of each slot
     const int32_t* ch_slot;  // [n_chunks]
     const int32_t* ch_start; // [n_chunks] first position of the chunk inside its row
+    const int32_t* sc_slot;  // [n_super] histogram blocks: slot
+    const int32_t* sc_start; // [n_super] first position
     int n_slots;
     int n_chunks;
+    int n_super;
 };
 
 struct SplitState {  // per (slot, column) selection state and scratch
@@ -264,6 +349,7 @@ struct ChunkInfo {
     int len;
 };
 
+template <int F>
 __device__ __forceinline__ ChunkInfo chunk_info(const SplitPlan& sp, const Side& side, int c) {
     ChunkInfo ci;
     ci.slot = sp.ch_slot[c];
@@ -271,7 +357,7 @@ __device__ __forceinline__ ChunkInfo chunk_info(const SplitPlan& sp, const Side&
     ci.lo = side.indptr[row];
     ci.n = (int)(side.indptr[row + 1] - ci.lo);
     ci.start = sp.ch_start[c];
-    ci.len = min(kSplitChunk, ci.n - ci.start);
+    ci.len = min(SplitChunk<F>::value, ci.n - ci.start);
     return ci;
 }
 
@@ -295,27 +381,43 @@ __global__ void k_split_init(Side side, Params p, SplitPlan sp, SplitState st) {
 template <int F>
 __global__ void __launch_bounds__(kCtaThreads) k_split_hist(Side side, Params p, SplitPlan sp, SplitState st,
                                                             int pass) {
-    __shared__ uint32_t hist[F][256];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    uint32_t (*hist)[kHistRow] = reinterpret_cast<uint32_t (*)[kHistRow]>(smem_raw);
     const int tid = threadIdx.x;
-    const ChunkInfo ci = chunk_info(sp, side, blockIdx.x);
-    for (int e = tid; e < F * 256; e += kCtaThreads) (&hist[0][0])[e] = 0u;
+    const int slot = sp.sc_slot[blockIdx.x];
+    const int64_t row = sp.row[slot];
+    const int64_t lo = side.indptr[row];
+    const int n = (int)(side.indptr[row + 1] - lo);
+    const int start = sp.sc_start[blockIdx.x];
+    const int len = min(kSplitSuper, n - start);
+    for (int e = tid; e < F * kHistRow; e += kCtaThreads) (&hist[0][0])[e] = 0u;
     __syncthreads();
     const int a_t = tid % F, k0 = tid / F;
     constexpr int kstep = kCtaThreads / F;
-    const int sa = ci.slot * F + a_t;
+    const int sa = slot * F + a_t;
     if (!st.done[sa]) {
         const uint32_t Pa = st.P[sa], hm = radix_before(pass);
-        const int64_t e0 = ci.lo + ci.start;
-        for (int k = k0; k < ci.len; k += kstep) {
-            const int32_t j = side.indices[e0 + k];
-            const uint32_t key = mag_key(__ldg(side.Y + (int64_t)j * p.f + a_t));
-            if ((key & hm) == Pa) atomicAdd(&hist[a_t][radix_digit(key, pass)], 1u);
+        const int64_t e0 = lo + start;
+        for (int kb = k0; kb < len; kb += kstep * kGatherBatch) {
+            int32_t j[kGatherBatch];
+            uint32_t key[kGatherBatch];
+#pragma unroll
+            for (int u = 0; u < kGatherBatch; ++u) {
+                const int k = kb + u * kstep;
+                j[u] = k < len ? side.indices[e0 + k] : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < kGatherBatch; ++u)
+                key[u] = j[u] >= 0 ? mag_key(__ldg(side.Y + (int64_t)j[u] * p.f + a_t)) : 0u;
+#pragma unroll
+            for (int u = 0; u < kGatherBatch; ++u)
+                if (j[u] >= 0 && (key[u] & hm) == Pa) atomicAdd(&hist[a_t][hist_slot(radix_digit(key[u], pass))], 1u);
         }
     }
     __syncthreads();
-    uint32_t* g = st.ghist + (int64_t)ci.slot * F * 256;
+    uint32_t* g = st.ghist + (int64_t)slot * F * 256;
     for (int e = tid; e < F * 256; e += kCtaThreads) {
-        const uint32_t v = (&hist[0][0])[e];
+        const uint32_t v = hist[e >> 8][hist_slot(e & 255)];
         if (v) atomicAdd(g + e, v);
     }
 }
@@ -328,9 +430,7 @@ __global__ void k_split_scan(SplitPlan sp, SplitState st, int pass) {
     if (e >= sp.n_slots * F) return;
     if (st.done[e]) return;
     uint32_t* bins = st.ghist + (int64_t)e * 256;
-    const BinPick bp = warp_pick_bin(bins, (uint32_t)st.need[e]);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) bins[lane * 8 + q] = 0u;
+    const BinPick bp = warp_pick_bin<false>(bins, (uint32_t)st.need[e], true);
     if (lane == 0) {
         st.P[e] |= (uint32_t)bp.digit << radix_shift(pass);
         st.Mk[e] = radix_after(pass);
@@ -344,7 +444,7 @@ template <int F>
 __global__ void __launch_bounds__(kCtaThreads) k_split_eqcount(Side side, Params p, SplitPlan sp, SplitState st) {
     __shared__ int cnt[F];
     const int tid = threadIdx.x;
-    const ChunkInfo ci = chunk_info(sp, side, blockIdx.x);
+    const ChunkInfo ci = chunk_info<F>(sp, side, blockIdx.x);
     if (tid < F) cnt[tid] = 0;
     __syncthreads();
     const int a_t = tid % F, k0 = tid / F;
@@ -385,7 +485,7 @@ __global__ void k_split_cut(Side side, Params p, SplitPlan sp, SplitState st) {
     }
     int cut = 0x7fffffff;
     if (cstar >= 0) {
-        const ChunkInfo ci = chunk_info(sp, side, cstar);
+        const ChunkInfo ci = chunk_info<F>(sp, side, cstar);
         const int64_t e0 = ci.lo + ci.start;
         int seen = cum;
         for (int kb = 0; kb < ci.len; kb += 32) {
@@ -406,54 +506,40 @@ __global__ void k_split_cut(Side side, Params p, SplitPlan sp, SplitState st) {
     if (lane == 0) st.cut[e] = cut;
 }
 
-template <int F>
+template <int F, int ENG>
 struct SplitGramSmem {
-    float x[kSplitChunk][F];
-    float r[kSplitChunk];
-    int32_t idx[kSplitChunk];
-    uint32_t mask[kSplitChunk];
-    float Gp[kCtaWarps][F][F + 1];
+    static constexpr int CH = SplitChunk<F>::value;
+    static constexpr int W = MaskWords<F>::value;
+    float x[CH][F];
+    float r[CH];
+    int32_t idx[CH];
+    uint32_t mask[CH][W];
+    __align__(1024) uint8_t u[GramScratch<F, ENG>::value];
+    uint64_t bar;
+    uint32_t tmem_slot;
 };
 
 // Masked Gram of one chunk into part[c] (or masks only when mode == 2).
-template <int F>
+template <int F, int ENG>
 __global__ void __launch_bounds__(kCtaThreads) k_split_gram(Side side, Params p, SplitPlan sp, SplitState st,
                                                             int mode, uint32_t* __restrict__ masks_out) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SplitGramSmem<F>& S = *reinterpret_cast<SplitGramSmem<F>*>(smem_raw);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    using Smem = SplitGramSmem<F, ENG>;
+    Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+    constexpr int W = Smem::W;
+    const int tid = threadIdx.x;
     const int c = blockIdx.x;
-    const ChunkInfo ci = chunk_info(sp, side, c);
+    const ChunkInfo ci = chunk_info<F>(sp, side, c);
     stage_tile<F>(S.x, S.r, S.idx, side, p.f, ci.lo + ci.start, ci.len);
-    const int a_t = tid % F, k0 = tid / F;
-    constexpr int kstep = kCtaThreads / F;
-    const int sa = ci.slot * F + a_t;
-    const uint32_t Pa = st.P[sa], Ma = st.Mk[sa];
-    const int cuta = st.cut[sa];
-    const uint32_t fmask = (F == 32) ? kFull : ((1u << F) - 1u);
-    for (int kk = 0; kk < ci.len; kk += kstep) {
-        const int k = kk + k0;
-        const bool keep = k < ci.len && keep_rule(mag_key(S.x[k][a_t]), Pa, Ma, ci.start + k, cuta);
-        const unsigned b = __ballot_sync(kFull, keep);
-        if (a_t == 0 && k < ci.len) S.mask[k] = (b >> (lane & ~(F - 1))) & fmask;
-    }
+    const int sa = ci.slot * F + tid % F;
+    build_masks<F>(S.mask, S.x, ci.len, ci.start, st.P[sa], st.Mk[sa], st.cut[sa]);
     __syncthreads();
     if (masks_out != nullptr)
-        for (int k = tid; k < ci.len; k += kCtaThreads) masks_out[ci.lo + ci.start + k] = S.mask[k];
+        for (int e = tid; e < ci.len * W; e += kCtaThreads) masks_out[(ci.lo + ci.start) * W + e] = (&S.mask[0][0])[e];
     if (mode == 2) return;
-    GramAcc<F> g;
-    g.zero();
-    g.add_tile(S.x, S.mask, S.r, warp, ci.len, kCtaWarps, p.gram_mode == GRAM_SYM);
-    g.store(S.Gp[warp]);
-    __syncthreads();
     float* dst = st.part + (int64_t)c * F * (F + 1);
-    for (int e = tid; e < F * (F + 1); e += kCtaThreads) {
-        const int a = e / (F + 1), b = e % (F + 1);
-        float v = 0.f;
-#pragma unroll
-        for (int q = 0; q < kCtaWarps; ++q) v += S.Gp[q][a][b];
-        dst[e] = v;
-    }
+    gram_tile<F, ENG>(S.u, &S.bar, &S.tmem_slot, S.x, S.mask, S.r, ci.len, p.gram_mode == GRAM_SYM,
+                      [&](int a, int cc, float v) { dst[a * (F + 1) + cc] = v; });
 }
 
 // Sum the chunk Grams of each slot in chunk order, add the regulariser.

@@ -60,6 +60,9 @@ def test_option_validation_without_gpu(lib):
     bad.budget = 1.5
     assert lib.als_create(ctypes.byref(h), ctypes.byref(bad), None) == -1
     bad = B.als_options.from_buffer_copy(opt)
-    bad.n_f = 64
+    bad.n_f = 129
     assert lib.als_create(ctypes.byref(h), ctypes.byref(bad), None) == -8
+    bad = B.als_options.from_buffer_copy(opt)
+    bad.precision = 7
+    assert lib.als_create(ctypes.byref(h), ctypes.byref(bad), None) == -1
     assert lib.als_create(None, ctypes.byref(opt), None) == -1

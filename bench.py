@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--precision", choices=["fp32", "tf32", "bf16", "fp32_tc"], default="fp32")
     return ap.parse_args()
 
 
@@ -58,7 +59,7 @@ def workload_config(w, r):
     return {"workload": f"{WORKLOAD}: {w['n_u']} users x {w['n_m']} items, {w['nnz']} observed "
                         f"(Zipf {w['zipf_s']}), n_f={w['f']}, lambda={w['lam']}, r={r}, asymmetric Eq. core_ui",
             "n_u": w["n_u"], "n_m": w["n_m"], "nnz": w["nnz"], "n_f": w["f"], "lambda": w["lam"], "budget": r,
-            "gram": "asym", "reg": "weighted", "train_frac": 0.9}
+            "gram": "asym", "reg": "weighted", "train_frac": 0.9, "precision": "fp32"}
 
 
 # ----------------------------------------------------------------- clocks
@@ -167,7 +168,7 @@ def gpu_arm(args, p, w, M0, r, rank, world, local_rank):
     Ru = core_als.DeviceCSR.from_host(p.train_rows, dev)
     Ri = core_als.DeviceCSR.from_host(p.train_cols, dev)
     tu, tm, tr = (torch.as_tensor(a).to(dev) for a in (p.test_u, p.test_m, p.test_r))
-    eng = core_als.CoreALS(f, lam, r, gram_mode="asym")
+    eng = core_als.CoreALS(f, lam, r, gram_mode="asym", precision=PRECISIONS[args.precision])
     eng.prepare(Ru)
     eng.prepare(Ri)
     M = torch.as_tensor(M0).to(dev)
@@ -202,7 +203,7 @@ def gpu_arm(args, p, w, M0, r, rank, world, local_rank):
     launches = eng.launch_count - launches0
     ms = sum(a.elapsed_time(b) for a, b in evs)
     fam = {}
-    for name in ("cta_rows", "warp_rows", "solve_rows", "sse", "sum_partials"):
+    for name in KERNEL_FAMILIES:
         t, n = eng.kernel_time(name)
         if n:
             fam[name] = (t, n)
@@ -227,7 +228,8 @@ def gpu_arm(args, p, w, M0, r, rank, world, local_rank):
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Zipf rating matrix; no dataset)",
+           "vs_baseline": None, "dtype": {"fp32": "f32", "fp32_tc": "f32 (split tf32)", "tf32": "tf32/f32",
+                                          "bf16": "bf16/f32"}[args.precision], "data": "synthetic (seeded Zipf rating matrix; no dataset)",
            "config": dict(workload_config(w, r), l2="flushed between steps (256 MB write)",
                           parallelism="replicas" if world > 1 else "single GPU"),
            "gpu_launches": launches, "roofline": roof, "clocks": clk.summary(),
@@ -236,20 +238,32 @@ def gpu_arm(args, p, w, M0, r, rank, world, local_rank):
     return out, eng, (Ru, Ri, tu, tm, tr), dev
 
 
+KERNEL_FAMILIES = ("cta_rows", "warp_rows", "solve_rows", "split_init", "split_hist", "split_scan", "split_eqcount",
+                   "split_cut", "split_gram", "split_reduce", "sse", "sum_partials")
+
+
 def roofline(top, avg_s, p, f, r):
     """Roofline entry of the dominant kernel family: algorithmic FP32 flops
     of the rows it handles (2 s_i f^2 for X*^T X plus 2 s_i f for X*^T r, with
-    s_i = floor(n_i r)), averaged over its two launches per sweep."""
+    s_i = floor(n_i r)), per launch (cta_rows: 3 bucket launches per side)."""
     flops = 0.0
+    launches_per_sweep = {"cta_rows": 6, "warp_rows": 1, "split_gram": 2}.get(top, 2)
     for csr in (p.train_rows, p.train_cols):
         L = np.diff(csr.indptr)
-        sel = L > 32 if top in ("cta_rows", "solve_rows") else L <= 32
+        if top == "cta_rows":
+            sel = (L > 32) & (L <= 1024)
+        elif top == "warp_rows":
+            sel = L <= 32
+        elif top in ("split_gram", "split_hist"):
+            sel = L > 1024
+        else:
+            sel = L > 32
         s = np.floor(L[sel].astype(np.float64) * r)
         if top == "solve_rows":
             flops += sel.sum() * (2.0 / 3.0 * f ** 3 + 2 * f * f)
         else:
             flops += float((2 * s * f * f + 2 * s * f).sum())
-    per_launch = flops / 2.0
+    per_launch = flops / launches_per_sweep
     achieved = per_launch / avg_s / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP32_ALU_PEAK_TFLOPS, "traffic": None, "kernel": top,
@@ -287,6 +301,9 @@ def e2e_leg(p, w, r, M0, steps=3):
             "d2h_bytes_per_step": int(d2h), "api": "als_fit_host (1 sweep per call, incl. validation)"}
 
 
+PRECISIONS = {"fp32": 0, "tf32": 1, "bf16": 2, "fp32_tc": 3}
+
+
 def variants(p, w, M0, rvals, steps=5):
     """Rows/s of other estimator settings on the same workload (device-timed)."""
     import torch
@@ -294,8 +311,8 @@ def variants(p, w, M0, rvals, steps=5):
     Ru = core_als.DeviceCSR.from_host(p.train_rows)
     Ri = core_als.DeviceCSR.from_host(p.train_cols)
     out = {}
-    for name, r, mode in rvals:
-        eng = core_als.CoreALS(w["f"], w["lam"], r, gram_mode=mode)
+    for name, r, mode, prec in rvals:
+        eng = core_als.CoreALS(w["f"], w["lam"], r, gram_mode=mode, precision=PRECISIONS[prec])
         M = torch.as_tensor(M0).cuda()
         U = torch.empty((p.n_u, w["f"]), dtype=torch.float32, device="cuda")
         for _ in range(2):
@@ -312,6 +329,45 @@ def variants(p, w, M0, rvals, steps=5):
         out[name] = (p.n_u + p.n_m) * steps / (a.elapsed_time(b) / 1e3)
         eng.close()
     return out
+
+
+def time_to_rmse(p, w, M0, settings, sweeps=15):
+    """Algorithm 2 from the same M^(0) for each setting: the test RMSE after
+    every sweep and the cumulative CUDA-event sweep time. The target is the
+    first setting's final test RMSE x (1 + 1e-3); each setting reports the
+    time of the first sweep that reaches it (None if it never does)."""
+    import torch
+    from paper_2509_18024_gb300 import core_als
+    Ru = core_als.DeviceCSR.from_host(p.train_rows)
+    Ri = core_als.DeviceCSR.from_host(p.train_cols)
+    tu, tm, tr = (torch.as_tensor(a).cuda() for a in (p.test_u, p.test_m, p.test_r))
+    curves = {}
+    for name, r, mode, prec in settings:
+        eng = core_als.CoreALS(w["f"], w["lam"], r, gram_mode=mode, precision=PRECISIONS[prec])
+        eng.prepare(Ru)
+        eng.prepare(Ri)
+        M = torch.as_tensor(M0).cuda()
+        U = torch.empty((p.n_u, w["f"]), dtype=torch.float32, device="cuda")
+        cum, pts = 0.0, []
+        for _ in range(sweeps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            eng.half_sweep(Ru, M, U)
+            eng.half_sweep(Ri, U, M)
+            b.record()
+            torch.cuda.synchronize()
+            cum += a.elapsed_time(b)
+            pts.append((cum, eng.rmse(tu, tm, tr, U, M)))
+        curves[name] = pts
+        eng.close()
+    first = settings[0][0]
+    target = curves[first][-1][1] * (1 + 1e-3)
+    res = {"target_rmse": target, "target_from": first, "sweeps": sweeps}
+    for name, pts in curves.items():
+        hit = next((t for t, e in pts if e <= target), None)
+        res[name] = {"ms": hit, "final_rmse": pts[-1][1], "sweeps_to_target":
+                     next((q + 1 for q, (t, e) in enumerate(pts) if e <= target), None)}
+    return res
 
 
 def main():
@@ -341,8 +397,14 @@ def main():
         out, eng, _, _ = res
         out["e2e"] = e2e_leg(p, w, r, M0)
         if not args.no_variants:
-            out["variants_rows_per_s"] = variants(p, w, M0, [("full_als", 1.0, "full"), ("core_r0.10", 0.10, "asym"),
-                                                             ("core_r0.50", 0.50, "asym")])
+            out["variants_rows_per_s"] = variants(p, w, M0, [
+                ("full_als_fp32", 1.0, "full", "fp32"), ("core_r0.10_fp32", 0.10, "asym", "fp32"),
+                ("core_r0.50_fp32", 0.50, "asym", "fp32"), ("core_r0.25_fp32_tc", r, "asym", "fp32_tc"),
+                ("core_r0.25_tf32", r, "asym", "tf32"), ("core_r0.25_bf16", r, "asym", "bf16"),
+                ("full_als_bf16", 1.0, "full", "bf16")])
+            out["time_to_rmse"] = time_to_rmse(p, w, M0, [
+                ("core_fp32", r, "asym", "fp32"), ("core_tf32", r, "asym", "tf32"), ("core_bf16", r, "asym", "bf16"),
+                ("core_fp32_tc", r, "asym", "fp32_tc"), ("full_fp32", 1.0, "full", "fp32")])
         if world == 1 and not args.no_cpu_baseline:
             rate, done, t_sweep = oracle_sample(p, M0, w["lam"], r, 40000, 8000, 7)
             import oracle

@@ -289,6 +289,56 @@ __device__ __forceinline__ BinPick warp_pick_bin(uint32_t* bins, uint32_t need, 
     return r;
 }
 
+// ---------------------------------------------------------------------------
+// 64-bin selection passes (CTA-resident rows). Exponent passes use a window
+// of 63 exponents [T-63, T-1] below an exclusive top T (bins 1..63) plus one
+// bin for everything below (bin 0); mantissa passes take 6 bits at a time
+// (bits 22..17, 16..11, 10..5, 4..0). Bin b of column a sits at
+// a * kHist64Row + b + b / 32: conflict-free both for 32 columns hitting one
+// bin (bank 3a + ...) and for a lane reading bins 2l, 2l + 1.
+constexpr int kHist64Row = 67;
+__device__ __forceinline__ int hist64_slot(int b) { return b + (b >> 5); }
+__device__ __forceinline__ int man_shift(int m) { return m == 0 ? 17 : (m == 1 ? 11 : (m == 2 ? 5 : 0)); }
+__device__ __forceinline__ uint32_t man_before(int m) {
+    return m == 0 ? 0xff800000u : (m == 1 ? 0xfffe0000u : (m == 2 ? 0xfffff800u : 0xffffffe0u));
+}
+__device__ __forceinline__ uint32_t man_after(int m) {
+    return m == 0 ? 0xfffe0000u : (m == 1 ? 0xfffff800u : (m == 2 ? 0xffffffe0u : 0xffffffffu));
+}
+
+// Warp scan of 64 bins from the top (lane l holds bins 2l, 2l + 1), clearing
+// them: the bin where the running count first reaches `need` (>= 1).
+__device__ __forceinline__ BinPick warp_pick_bin64(uint32_t* bins, uint32_t need) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t c0 = bins[hist64_slot(2 * lane)], c1 = bins[hist64_slot(2 * lane + 1)];
+    bins[hist64_slot(2 * lane)] = 0u;
+    bins[hist64_slot(2 * lane + 1)] = 0u;
+    const uint32_t lsum = c0 + c1;
+    uint32_t incl = lsum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_down_sync(kFull, incl, o);
+        if (lane + o < 32) incl += t;
+    }
+    const uint32_t above = incl - lsum;
+    const unsigned ob = __ballot_sync(kFull, above < need && need <= incl);
+    const int L = ob ? __ffs(ob) - 1 : 0;
+    BinPick r;
+    if (above + c1 >= need) {
+        r.digit = 2 * lane + 1;
+        r.newneed = need - above;
+        r.inbin = c1;
+    } else {
+        r.digit = 2 * lane;
+        r.newneed = need - above - c1;
+        r.inbin = c0;
+    }
+    r.digit = __shfl_sync(kFull, r.digit, L);
+    r.newneed = __shfl_sync(kFull, r.newneed, L);
+    r.inbin = __shfl_sync(kFull, r.inbin, L);
+    return r;
+}
+
 // Keep rule of one column after selection: (key & Mk) > P, or equal to P on
 // the covered bits and at a position below cut.
 __device__ __forceinline__ bool keep_rule(uint32_t key, uint32_t P, uint32_t Mk, int pos, int cut) {

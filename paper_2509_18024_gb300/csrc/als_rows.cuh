@@ -196,7 +196,7 @@ __device__ __forceinline__ void gram_tile(uint8_t* scratch, uint64_t* bar, uint3
 template <int F, int NS, int ENG>
 struct CtaSmem {
     static constexpr int W = MaskWords<F>::value;
-    static constexpr int HIST_BYTES = F * kHistRow * 4;
+    static constexpr int HIST_BYTES = F * kHist64Row * 4;
     static constexpr int GRAM_BYTES = GramScratch<F, ENG>::value;
     static constexpr int U_BYTES = HIST_BYTES > GRAM_BYTES ? HIST_BYTES : GRAM_BYTES;
     float x[NS][F];
@@ -211,8 +211,9 @@ struct CtaSmem {
     int32_t need[F];
     int32_t cut[F];
     int32_t done[F];
-    int32_t open_after[4];  // columns still open after each pass
-    __device__ uint32_t (*hist())[kHistRow] { return reinterpret_cast<uint32_t (*)[kHistRow]>(u); }
+    int32_t eres[F];   // exponent of the threshold resolved
+    uint32_t wtop[F];  // exclusive exponent top of the next window pass
+    __device__ uint32_t (*hist())[kHist64Row] { return reinterpret_cast<uint32_t (*)[kHist64Row]>(u); }
 };
 
 // mode 0/1: write the augmented system of list entry w to G_aug[w]; mode 2:
@@ -236,7 +237,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_cta_rows(Side side, Params p, c
     const int a_t = tid % F;  // thread t always handles column t mod F
     const int k0 = tid / F;
     constexpr int kstep = kCtaThreads / F;
-    uint32_t (*hist)[kHistRow] = S.hist();
+    uint32_t (*hist)[kHist64Row] = S.hist();
 
     if (tid < F) {
         uint32_t P, Mk;
@@ -247,36 +248,80 @@ __global__ void __launch_bounds__(kCtaThreads) k_cta_rows(Side side, Params p, c
         S.need[tid] = need;
         S.cut[tid] = cut;
         S.done[tid] = done;
+        S.eres[tid] = 0;
+        S.wtop[tid] = 0u;
     }
-    if (tid < 4) S.open_after[tid] = 0;
     // Histograms start at zero; each scan re-zeroes the bins it read.
-    for (int e = tid; e < F * kHistRow; e += kCtaThreads) (&hist[0][0])[e] = 0u;
+    for (int e = tid; e < F * kHist64Row; e += kCtaThreads) (&hist[0][0])[e] = 0u;
     stage_tile<F>(S.x, S.r, S.idx, side, f, lo, n);
+    {
+        // Window top of each column: its largest exponent + 1.
+        uint32_t em = 0u;
+        for (int k = k0; k < n; k += kstep) em = max(em, mag_key(S.x[k][a_t]) >> 23);
+        atomicMax(&S.wtop[a_t], em + 1u);
+    }
+    __syncthreads();
 
-    bool active = f > 0 && s > 0 && s < n;
-    for (int pass = 0; pass < 4 && active; ++pass) {
-        const uint32_t hm = radix_before(pass);
+    // Exponent of the s-th largest key: windows of 63 exponents from the top.
+    bool more = __syncthreads_or(!S.done[a_t] && !S.eres[a_t]);
+    for (int it = 0; it < 5 && more; ++it) {
+        if (!S.done[a_t] && !S.eres[a_t]) {
+            const int T = (int)S.wtop[a_t];
+            for (int k = k0; k < n; k += kstep) {
+                const int E = (int)(mag_key(S.x[k][a_t]) >> 23);
+                if (E < T) atomicAdd(&hist[a_t][hist64_slot(E >= T - 63 ? E - T + 64 : 0)], 1u);
+            }
+        }
+        __syncthreads();
+        for (int a = warp; a < F; a += kCtaWarps) {
+            if (S.done[a] || S.eres[a]) continue;
+            const BinPick bp = warp_pick_bin64(hist[a], (uint32_t)S.need[a]);
+            if (lane == 0) {
+                const int T = (int)S.wtop[a];
+                if (bp.digit >= 1) {
+                    S.P[a] = (uint32_t)(T - 64 + bp.digit) << 23;
+                    S.Mk[a] = 0xff800000u;
+                    S.need[a] = (int)bp.newneed;
+                    S.eres[a] = 1;
+                    if (bp.inbin == bp.newneed) S.done[a] = 1;
+                } else if (bp.inbin == bp.newneed) {
+                    S.P[a] = 0u;  // everything below the window is kept too: keep all
+                    S.Mk[a] = 0u;
+                    S.done[a] = 1;
+                } else {
+                    S.wtop[a] = (uint32_t)(T - 63);
+                    S.need[a] = (int)bp.newneed;
+                }
+            }
+        }
+        __syncthreads();
+        more = __syncthreads_or(!S.done[a_t] && !S.eres[a_t]);
+    }
+    // Mantissa, 6 bits per pass, inside the resolved exponent.
+    more = __syncthreads_or(!S.done[a_t]);
+    for (int m = 0; m < 4 && more; ++m) {
+        const uint32_t hm = man_before(m);
+        const int sh = man_shift(m);
         if (!S.done[a_t]) {
             const uint32_t Pa = S.P[a_t];
             for (int k = k0; k < n; k += kstep) {
                 const uint32_t key = mag_key(S.x[k][a_t]);
-                if ((key & hm) == Pa) atomicAdd(&hist[a_t][hist_slot(radix_digit(key, pass))], 1u);
+                if ((key & hm) == Pa) atomicAdd(&hist[a_t][hist64_slot((key >> sh) & 63u)], 1u);
             }
         }
         __syncthreads();
         for (int a = warp; a < F; a += kCtaWarps) {
             if (S.done[a]) continue;
-            const BinPick bp = warp_pick_bin<true>(hist[a], (uint32_t)S.need[a], true);
+            const BinPick bp = warp_pick_bin64(hist[a], (uint32_t)S.need[a]);
             if (lane == 0) {
-                S.P[a] |= (uint32_t)bp.digit << radix_shift(pass);
-                S.Mk[a] = radix_after(pass);
+                S.P[a] |= (uint32_t)bp.digit << sh;
+                S.Mk[a] = man_after(m);
                 S.need[a] = (int)bp.newneed;
                 if (bp.inbin == bp.newneed) S.done[a] = 1;
-                else atomicAdd(&S.open_after[pass], 1);
             }
         }
         __syncthreads();
-        active = S.open_after[pass] > 0;
+        more = __syncthreads_or(!S.done[a_t]);
     }
     // Open columns: the full key P has more copies than places left; keep the
     // lowest positions.

@@ -81,6 +81,7 @@ extern "C" {
 /* Per-row flags written by the solve. */
 #define ALS_FLAG_RATIO 1     /* pivot ratio above pivot_ratio_max */
 #define ALS_FLAG_SINGULAR 2  /* zero / non-positive pivot: the row was set to 0 */
+#define ALS_FLAG_FP64 4      /* the row was re-assembled and re-solved in FP64 */
 
 typedef struct als_csr {
     int64_t n_rows;          /* rows of this side (users, or items for R^T) */
@@ -100,11 +101,17 @@ typedef struct als_options {
     int gram_mode;           /* ALS_GRAM_* */
     int precision;           /* ALS_FP32, ALS_TF32, ALS_BF16, ALS_FP32_TC */
     double pivot_ratio_max;  /* flag threshold on max pivot / min pivot, e.g. 1e6 */
+    int fp64_fallback;       /* 1: rows flagged by the FP32 solve (ratio above
+                                pivot_ratio_max, or a zero pivot) are
+                                re-assembled from the data and re-solved in
+                                FP64 (flag ALS_FLAG_FP64); 0: off */
+    int refine_steps;        /* iterative-refinement steps after the solve (0 or 1) */
 } als_options;
 
 typedef struct als_report {
     int64_t rows_flagged;     /* rows with ALS_FLAG_RATIO set, last half-sweep */
     int64_t rows_singular;    /* rows with ALS_FLAG_SINGULAR set, last half-sweep */
+    int64_t rows_fp64;        /* rows re-solved in FP64, last half-sweep */
     double max_pivot_ratio;   /* largest pivot ratio seen, last half-sweep */
     double test_rmse;         /* als_fit: test RMSE after the last sweep (NaN if no test set) */
     double objective;         /* als_fit: Eq. (object function) after the last sweep */
@@ -114,7 +121,8 @@ typedef struct als_report {
 typedef struct als_handle als_handle;
 
 /* Default options: n_f = 32, lambda = 0.05, budget = 0.25, weighted lambda,
- * asymmetric Gram, FP32, pivot_ratio_max = 1e6. */
+ * asymmetric Gram, FP32, pivot_ratio_max = 1e6, FP64 fallback on, no
+ * refinement. */
 void als_default_options(als_options* opt_host);
 
 /* Create a handle bound to the current CUDA device and to cuda_stream

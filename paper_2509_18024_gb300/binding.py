@@ -21,7 +21,7 @@ STATUS = {
 ALS_REG_WEIGHTED, ALS_REG_PLAIN = 0, 1
 ALS_GRAM_ASYM, ALS_GRAM_SYM, ALS_GRAM_FULL = 0, 1, 2
 ALS_FP32, ALS_TF32, ALS_BF16 = 0, 1, 2
-ALS_FLAG_RATIO, ALS_FLAG_SINGULAR = 1, 2
+ALS_FLAG_RATIO, ALS_FLAG_SINGULAR, ALS_FLAG_FP64 = 1, 2, 4
 ALS_SSE_STATIC_MAX_ENTRIES = 4096 * 16384
 
 
@@ -39,11 +39,12 @@ class als_csr(C.Structure):
 class als_options(C.Structure):
     _fields_ = [("n_f", C.c_int), ("lambda_", C.c_float), ("budget", C.c_double), ("min_keep", C.c_int64),
                 ("reg_mode", C.c_int), ("gram_mode", C.c_int), ("precision", C.c_int),
-                ("pivot_ratio_max", C.c_double)]
+                ("pivot_ratio_max", C.c_double), ("fp64_fallback", C.c_int), ("refine_steps", C.c_int)]
 
 
 class als_report(C.Structure):
-    _fields_ = [("rows_flagged", C.c_int64), ("rows_singular", C.c_int64), ("max_pivot_ratio", C.c_double),
+    _fields_ = [("rows_flagged", C.c_int64), ("rows_singular", C.c_int64), ("rows_fp64", C.c_int64),
+                ("max_pivot_ratio", C.c_double),
                 ("test_rmse", C.c_double), ("objective", C.c_double), ("sweeps_done", C.c_int)]
 
 

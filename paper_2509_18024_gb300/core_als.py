@@ -54,7 +54,7 @@ class CoreALS:
 
     def __init__(self, n_f: int, lam: float, budget: float, gram_mode: str = "asym",
                  reg_mode: str = "weighted", min_keep: int = 0, ratio_max: float = 1e6,
-                 precision: int = B.ALS_FP32):
+                 precision: int = B.ALS_FP32, fp64_fallback: bool = True, refine_steps: int = 0):
         _require_cuda()
         self.lib = B.load()
         opt = B.als_options()
@@ -67,6 +67,8 @@ class CoreALS:
         opt.gram_mode = GRAM_MODES[gram_mode]
         opt.precision = int(precision)
         opt.pivot_ratio_max = float(ratio_max)
+        opt.fp64_fallback = 1 if fp64_fallback else 0
+        opt.refine_steps = int(refine_steps)
         self.opt = opt
         self.n_f = int(n_f)
         h = C.c_void_p()

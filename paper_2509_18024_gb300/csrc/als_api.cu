@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "core_als.h"
+#include "als_fp64.cuh"
 #include "als_kernels.cuh"
 
 namespace {
@@ -95,6 +96,10 @@ struct als_handle {
     DevBuf g_aug;     // augmented systems of CTA rows
     DevBuf misc;      // counters + eval partials + error word
     DevBuf host_in;   // device copies for als_fit_host
+    DevBuf masks;     // CES masks of the current half-sweep (FP64 fallback)
+    DevBuf fb_list;   // rows flagged for the FP64 redo
+    DevBuf delta;     // refinement corrections
+    int n_sm = 152;
     int64_t launches = 0;
     std::string last_error;
     // Kernel timing (als_profile): events bracketing each launch.
@@ -233,6 +238,8 @@ int check_options(als_handle* h, const als_options* o) {
     if (o->precision < ALS_FP32 || o->precision > ALS_FP32_TC) return set_err(h, ALS_ERR_ARG, "bad precision");
     if (o->min_keep < 0) return set_err(h, ALS_ERR_ARG, "min_keep must be >= 0");
     if (!(o->pivot_ratio_max > 0.0)) return set_err(h, ALS_ERR_ARG, "pivot_ratio_max must be > 0");
+    if (o->fp64_fallback != 0 && o->fp64_fallback != 1) return set_err(h, ALS_ERR_ARG, "fp64_fallback must be 0 or 1");
+    if (o->refine_steps < 0 || o->refine_steps > 1) return set_err(h, ALS_ERR_ARG, "refine_steps must be 0 or 1");
     return ALS_OK;
 }
 
@@ -246,6 +253,8 @@ int check_csr(als_handle* h, const als_csr* R) {
 }
 
 Counters* counters(als_handle* h) { return reinterpret_cast<Counters*>(h->misc.p); }
+// Counters of the refinement's second solve (not reported).
+Counters* scratch_counters(als_handle* h) { return reinterpret_cast<Counters*>(reinterpret_cast<char*>(h->misc.p) + 128); }
 double* eval_partials(als_handle* h) {
     return reinterpret_cast<double*>(reinterpret_cast<char*>(h->misc.p) + 256);
 }
@@ -418,17 +427,31 @@ int launch_split(als_handle* h, const Plan& pl, const Side& side, const Params& 
 // Batched solve of augmented systems listed by `list` (null: identity).
 template <int F>
 int launch_solve(als_handle* h, const float* aug, const int32_t* list, int count, const Params& p, float* X_out,
-                 int32_t* flags_out) {
+                 int32_t* flags_out, als::Fallback fb, Counters* cnt = nullptr) {
     if (count == 0) return ALS_OK;
+    if (cnt == nullptr) cnt = counters(h);
     if constexpr (F <= 32) {
         ALS_LAUNCH(h, "solve_rows", als::k_solve_rows<F><<<(count + 7) / 8, 256, 0, h->stream>>>(
-                                        aug, list, count, p, X_out, flags_out, counters(h)));
+                                        aug, list, count, p, X_out, flags_out, cnt, fb));
     } else {
         const size_t smem = (size_t)F * (F + 1) * sizeof(float);
         ALS_CUDA(h, cudaFuncSetAttribute(als::k_solve_big<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         ALS_LAUNCH(h, "solve_rows", als::k_solve_big<F><<<count, als::kBigSolveThreads, smem, h->stream>>>(
-                                        aug, list, count, p, X_out, flags_out, counters(h)));
+                                        aug, list, count, p, X_out, flags_out, cnt, fb));
     }
+    return ALS_OK;
+}
+
+// FP64 redo of the rows the solves flagged (fixed grid; reads the list
+// length on the device).
+template <int F>
+int launch_fp64(als_handle* h, const Side& side, const Params& p, const uint32_t* masks, float* X_out,
+                int32_t* flags_out) {
+    const size_t smem = sizeof(als::Fp64Smem<F>);
+    ALS_CUDA(h, cudaFuncSetAttribute(als::k_fp64_rows<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ALS_LAUNCH(h, "fp64_rows", als::k_fp64_rows<F><<<h->n_sm, als::kFp64Threads, smem, h->stream>>>(
+                                   side, p, masks, reinterpret_cast<const int32_t*>(h->fb_list.p),
+                                   &counters(h)->fb_count, X_out, flags_out, counters(h)));
     return ALS_OK;
 }
 
@@ -450,6 +473,22 @@ int run_side(als_handle* h, const Plan& pl, const Side& side, int mode, float* X
     int rc = ensure(h, h->g_aug, (size_t)std::max(n_aug, 1) * F * (F + 1) * sizeof(float));
     if (rc) return rc;
     float* G_aug = reinterpret_cast<float*>(h->g_aug.p);
+    // FP64 fallback: keep the masks and collect the flagged rows.
+    als::Fallback fb{nullptr, nullptr};
+    const bool fallback = mode == 0 && h->opt.fp64_fallback != 0;
+    const bool refine = mode == 0 && h->opt.refine_steps > 0;
+    if (fallback || refine) {
+        constexpr int W = (F + 31) / 32;
+        rc = ensure(h, h->masks, (size_t)std::max<int64_t>(pl.nnz, 1) * W * sizeof(uint32_t));
+        if (rc) return rc;
+        rc = ensure(h, h->fb_list, (size_t)std::max<int64_t>(pl.n_rows, 1) * sizeof(int32_t));
+        if (rc) return rc;
+        if (masks_out == nullptr) masks_out = reinterpret_cast<uint32_t*>(h->masks.p);
+        if (fallback) {
+            fb.rows = reinterpret_cast<int32_t*>(h->fb_list.p);
+            fb.count = &counters(h)->fb_count;
+        }
+    }
     // Augmented systems: [split slots | bucket0 | bucket1 | bucket2] in G_aug.
     float* aug_split = G_aug;
     float* aug_b0 = aug_split + (size_t)pl.n_slots * F * (F + 1);
@@ -475,7 +514,7 @@ int run_side(als_handle* h, const Plan& pl, const Side& side, int mode, float* X
     for (const Seg& sg : segs) {
         if (sg.count == 0) continue;
         if (mode == 0) {
-            rc = launch_solve<F>(h, sg.aug, sg.list, sg.count, p, X_out, flags_out);
+            rc = launch_solve<F>(h, sg.aug, sg.list, sg.count, p, X_out, flags_out, fb);
             if (rc) return rc;
         } else if (mode == 1) {
             ALS_LAUNCH(h, "unpack_aug", als::k_unpack_aug<F><<<1024, 256, 0, st>>>(sg.aug, sg.list, sg.count, p.f,
@@ -486,11 +525,32 @@ int run_side(als_handle* h, const Plan& pl, const Side& side, int mode, float* X
         if (pl.n_warp > 0) {
             ALS_LAUNCH(h, "warp_rows", als::k_warp_rows<F><<<(pl.n_warp + 7) / 8, 256, 0, st>>>(
                                            side, p, lists, pl.n_warp, mode, X_out, flags_out, masks_out, G_aug,
-                                           counters(h)));
+                                           counters(h), fb));
             if (mode == 1)
                 ALS_LAUNCH(h, "unpack_aug", als::k_unpack_aug<F><<<1024, 256, 0, st>>>(G_aug, lists, pl.n_warp, p.f,
                                                                                         G_out, b_out));
         }
+    }
+    if (refine) {
+        // One refinement step for the CTA and split rows: residual from the
+        // data into the rhs column, second solve of the same G, X += delta.
+        rc = ensure(h, h->delta, (size_t)std::max<int64_t>(pl.n_rows, 1) * p.f * sizeof(float));
+        if (rc) return rc;
+        float* D = reinterpret_cast<float*>(h->delta.p);
+        for (const Seg& sg : segs) {
+            if (sg.count == 0) continue;
+            ALS_LAUNCH(h, "refine_resid", als::k_refine_resid<F><<<sg.count, als::kRefineThreads, 0, st>>>(
+                                              side, p, masks_out, sg.list, sg.count, sg.aug, X_out));
+            rc = launch_solve<F>(h, sg.aug, sg.list, sg.count, p, D, nullptr, als::Fallback{nullptr, nullptr},
+                                 scratch_counters(h));
+            if (rc) return rc;
+            ALS_LAUNCH(h, "add_rows", als::k_add_rows<<<std::min(1024, (sg.count * p.f + 255) / 256), 256, 0, st>>>(
+                                          sg.list, sg.count, p.f, D, X_out));
+        }
+    }
+    if (fallback) {
+        rc = launch_fp64<F>(h, side, p, masks_out, X_out, flags_out);
+        if (rc) return rc;
     }
     return ALS_OK;
 }
@@ -546,7 +606,7 @@ int solve_systems(als_handle* h, int64_t n_rows, const float* G, const float* b,
     float* G_aug = reinterpret_cast<float*>(h->g_aug.p);
     ALS_CUDA(h, cudaMemsetAsync(counters(h), 0, sizeof(Counters), st));
     ALS_LAUNCH(h, "pack_aug", als::k_pack_aug<F><<<1024, 256, 0, st>>>(G, b, n_rows, p.f, G_aug));
-    return launch_solve<F>(h, G_aug, nullptr, (int)n_rows, p, X_out, flags_out);
+    return launch_solve<F>(h, G_aug, nullptr, (int)n_rows, p, X_out, flags_out, als::Fallback{nullptr, nullptr});
 }
 
 }  // namespace
@@ -564,6 +624,8 @@ void als_default_options(als_options* o) {
     o->gram_mode = ALS_GRAM_ASYM;
     o->precision = ALS_FP32;
     o->pivot_ratio_max = 1e6;
+    o->fp64_fallback = 1;
+    o->refine_steps = 0;
 }
 
 int als_create(als_handle** out, const als_options* opt, void* stream) {
@@ -578,6 +640,10 @@ int als_create(als_handle** out, const als_options* opt, void* stream) {
         cudaGetLastError();
         delete h;
         return ALS_ERR_CUDA;
+    }
+    if (cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || h->n_sm <= 0) {
+        cudaGetLastError();
+        h->n_sm = 152;
     }
     rc = ensure(h, h->misc, kMiscBytes);
     if (rc) {
@@ -603,7 +669,7 @@ int als_destroy(als_handle* h) {
         cudaEventDestroy(t.stop);
     }
     for (auto e : h->event_pool) cudaEventDestroy(e);
-    for (DevBuf* b : {&h->g_aug, &h->misc, &h->host_in})
+    for (DevBuf* b : {&h->g_aug, &h->misc, &h->host_in, &h->masks, &h->fb_list, &h->delta})
         if (b->p) cudaFree(b->p);
     delete h;
     return ALS_OK;
@@ -732,6 +798,7 @@ int als_get_report(als_handle* h, als_report* rep) {
     std::memset(rep, 0, sizeof *rep);
     rep->rows_flagged = (int64_t)c.flagged;
     rep->rows_singular = (int64_t)c.singular;
+    rep->rows_fp64 = (int64_t)c.fp64_rows;
     float mr;
     std::memcpy(&mr, &c.max_ratio_bits, sizeof mr);
     rep->max_pivot_ratio = mr;
@@ -836,7 +903,7 @@ int als_fit_host(als_handle* h, int64_t n_u, int64_t n_m, int64_t nnz, const int
 
 int64_t als_workspace_bytes(const als_handle* h) {
     if (!h) return 0;
-    int64_t b = (int64_t)(h->g_aug.bytes + h->misc.bytes + h->host_in.bytes);
+    int64_t b = (int64_t)(h->g_aug.bytes + h->misc.bytes + h->host_in.bytes + h->masks.bytes + h->fb_list.bytes);
     for (const auto& p : h->plans)
         b += (int64_t)SplitLayout(p.n_slots, p.n_chunks, p.F).total +
              (int64_t)(p.n_rows + 2 * p.n_chunks + 2 * p.n_super + p.n_slots + 1) * 4;

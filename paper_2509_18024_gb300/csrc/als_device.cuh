@@ -14,7 +14,7 @@ namespace als {
 
 enum { GRAM_ASYM = 0, GRAM_SYM = 1, GRAM_FULL = 2 };
 enum { REG_WEIGHTED = 0, REG_PLAIN = 1 };
-enum { FLAG_RATIO = 1, FLAG_SINGULAR = 2 };
+enum { FLAG_RATIO = 1, FLAG_SINGULAR = 2, FLAG_FP64 = 4 };
 
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -43,6 +43,16 @@ struct Counters {
     unsigned long long singular;
     unsigned int max_ratio_bits;  // float bits of the largest finite pivot ratio
     unsigned int error;           // device-side error word (0 = none)
+    unsigned long long fp64_rows; // rows re-solved in FP64
+    unsigned int fb_count;        // entries in the FP64 fallback list
+    unsigned int pad;
+};
+
+// Rows whose FP32 solve was flagged are appended here for the FP64 redo
+// (rows == nullptr: fallback off).
+struct Fallback {
+    int32_t* rows;
+    unsigned int* count;
 };
 
 // |x| as an order-preserving unsigned key: for finite floats the unsigned
@@ -344,6 +354,10 @@ __device__ __forceinline__ BinPick warp_pick_bin64(uint32_t* bins, uint32_t need
 __device__ __forceinline__ bool keep_rule(uint32_t key, uint32_t P, uint32_t Mk, int pos, int cut) {
     const uint32_t kc = key & Mk;
     return kc > P || (kc == P && pos < cut);
+}
+
+__device__ __forceinline__ void fallback_push(const Fallback& fb, int flags, int64_t row) {
+    if (fb.rows != nullptr && flags != 0) fb.rows[atomicAdd(fb.count, 1u)] = (int32_t)row;
 }
 
 __device__ __forceinline__ void record_flags(Counters* c, int flags, float ratio) {

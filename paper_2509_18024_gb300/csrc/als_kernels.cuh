@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(256) k_warp_rows(Side side, Params p, const in
                                                    int n_list, int mode, float* __restrict__ X_out,
                                                    int32_t* __restrict__ flags_out,
                                                    uint32_t* __restrict__ masks_out,
-                                                   float* __restrict__ G_aug, Counters* cnt) {
+                                                   float* __restrict__ G_aug, Counters* cnt, Fallback fb) {
     __shared__ WarpRowTile<F> tiles[8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int w = blockIdx.x * 8 + warp;
@@ -142,6 +142,7 @@ __global__ void __launch_bounds__(256) k_warp_rows(Side side, Params p, const in
     if (lane == 0) {
         if (flags_out) flags_out[i] = flags;
         record_flags(cnt, flags, ratio);
+        fallback_push(fb, flags, i);
     }
 }
 
@@ -158,7 +159,7 @@ namespace als {
 template <int F>
 __global__ void __launch_bounds__(256) k_solve_rows(const float* __restrict__ G_aug, const int32_t* __restrict__ rows,
                                                     int n_list, Params p, float* __restrict__ X_out,
-                                                    int32_t* __restrict__ flags_out, Counters* cnt) {
+                                                    int32_t* __restrict__ flags_out, Counters* cnt, Fallback fb) {
     __shared__ float tile[8][F][F + 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int w = blockIdx.x * 8 + warp;
@@ -179,42 +180,29 @@ __global__ void __launch_bounds__(256) k_solve_rows(const float* __restrict__ G_
     if (lane == 0) {
         if (flags_out) flags_out[i] = flags;
         record_flags(cnt, flags, ratio);
+        fallback_push(fb, flags, i);
     }
 }
 
-// Batched solve for widths above 32 (F = 64, 128): one CTA of 128 threads per
-// system held in shared memory, right-looking elimination with partial
-// pivoting (asymmetric form) or diagonal pivots (symmetric modes), then
-// column-oriented back substitution. Same flags and pivot ratio as k_solve_rows.
-constexpr int kBigSolveThreads = 128;
-
-template <int F>
-__global__ void __launch_bounds__(kBigSolveThreads) k_solve_big(const float* __restrict__ G_aug,
-                                                               const int32_t* __restrict__ rows, int n_list,
-                                                               Params p, float* __restrict__ X_out,
-                                                               int32_t* __restrict__ flags_out, Counters* cnt) {
-    extern __shared__ float smem_f[];
-    float (*A)[F + 1] = reinterpret_cast<float (*)[F + 1]>(smem_f);
-    __shared__ int s_piv;
-    __shared__ float s_x[F];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int w = blockIdx.x;
-    if (w >= n_list) return;
-    const float* src = G_aug + (int64_t)w * F * (F + 1);
-    for (int e = tid; e < F * (F + 1); e += kBigSolveThreads) (&A[0][0])[e] = src[e];
-    __syncthreads();
-    const bool pivot = p.gram_mode == GRAM_ASYM;
-    const int f = p.f;
-    float pmax = 0.f, pmin = __int_as_float(0x7f800000);
+// CTA-wide elimination on an augmented system A = [G | b] (F x (F+1), type T,
+// shared memory), rows >= f padding: right-looking with partial pivoting
+// (`pivot`) or diagonal pivots, then column-oriented back substitution into
+// xs. All threads of the CTA call it. Returns flags; ratio = max/min pivot
+// over the first f pivots.
+template <typename T, int F>
+__device__ __forceinline__ int cta_lu_solve(T (*A)[F + 1], T* xs, int* s_piv, int f, bool pivot, float ratio_max,
+                                            float& ratio_out) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nt = blockDim.x;
+    T pmax = 0, pmin = (T)INFINITY;
     bool singular = false;
     for (int k = 0; k < F; ++k) {
         if (warp == 0) {
             int bi = k;
             if (pivot) {
-                float best = -1.f;
+                T best = -1;
                 bi = F;
                 for (int i = k + lane; i < F; i += 32) {
-                    const float v = fabsf(A[i][k]);
+                    const T v = A[i][k] < 0 ? -A[i][k] : A[i][k];
                     if (v > best) {
                         best = v;
                         bi = i;
@@ -222,7 +210,7 @@ __global__ void __launch_bounds__(kBigSolveThreads) k_solve_big(const float* __r
                 }
 #pragma unroll
                 for (int o = 16; o; o >>= 1) {
-                    const float ob = __shfl_xor_sync(kFull, best, o);
+                    const T ob = __shfl_xor_sync(kFull, best, o);
                     const int oi = __shfl_xor_sync(kFull, bi, o);
                     if (ob > best || (ob == best && oi < bi)) {
                         best = ob;
@@ -230,56 +218,84 @@ __global__ void __launch_bounds__(kBigSolveThreads) k_solve_big(const float* __r
                     }
                 }
             }
-            if (lane == 0) s_piv = bi;
+            if (lane == 0) *s_piv = bi;
         }
         __syncthreads();
-        const int pr = s_piv;
+        const int pr = *s_piv;
         if (pr != k)
-            for (int j = k + tid; j <= F; j += kBigSolveThreads) {
-                const float t = A[k][j];
+            for (int j = k + tid; j <= F; j += nt) {
+                const T t = A[k][j];
                 A[k][j] = A[pr][j];
                 A[pr][j] = t;
             }
         __syncthreads();
-        const float pv = A[k][k];
-        const float apv = pivot ? fabsf(pv) : pv;
+        const T pv = A[k][k];
+        const T apv = pivot ? (pv < 0 ? -pv : pv) : pv;
         if (k < f) {
-            if (!(apv > 0.f)) singular = true;
-            pmax = fmaxf(pmax, apv);
-            pmin = fminf(pmin, apv);
+            if (!(apv > 0)) singular = true;
+            pmax = apv > pmax ? apv : pmax;
+            pmin = apv < pmin ? apv : pmin;
         }
-        if (pv != 0.f) {
-            for (int i = k + 1 + tid; i < F; i += kBigSolveThreads) A[i][k] /= pv;
+        if (pv != (T)0) {
+            for (int i = k + 1 + tid; i < F; i += nt) A[i][k] /= pv;
             __syncthreads();
             const int cols = F - k;  // columns k+1 .. F (rhs included)
             const int total = (F - 1 - k) * cols;
-            for (int e = tid; e < total; e += kBigSolveThreads) {
+            for (int e = tid; e < total; e += nt) {
                 const int i = k + 1 + e / cols, j = k + 1 + e % cols;
-                A[i][j] = fmaf(-A[i][k], A[k][j], A[i][j]);
+                A[i][j] -= A[i][k] * A[k][j];
             }
         }
         __syncthreads();
     }
     for (int k = F - 1; k >= 0; --k) {
-        if (tid == 0) s_x[k] = A[k][F] / A[k][k];
+        if (tid == 0) xs[k] = A[k][F] / A[k][k];
         __syncthreads();
-        const float xk = s_x[k];
-        for (int i = tid; i < k; i += kBigSolveThreads) A[i][F] = fmaf(-A[i][k], xk, A[i][F]);
+        const T xk = xs[k];
+        for (int i = tid; i < k; i += nt) A[i][F] -= A[i][k] * xk;
         __syncthreads();
     }
     int flags = 0;
-    float ratio = (f > 0) ? pmax / pmin : 1.f;
+    ratio_out = (f > 0) ? (float)(pmax / pmin) : 1.f;
     if (singular) {
         flags = FLAG_SINGULAR | FLAG_RATIO;
-        ratio = __int_as_float(0x7f800000);
-    } else if (!(ratio <= p.ratio_max)) {
+        ratio_out = __int_as_float(0x7f800000);
+    } else if (!(ratio_out <= ratio_max)) {
         flags = FLAG_RATIO;
     }
+    return flags;
+}
+
+// Batched solve for widths above 32 (F = 64, 128): one CTA of 128 threads per
+// system held in shared memory (cta_lu_solve). Same flags and pivot ratio as
+// k_solve_rows.
+constexpr int kBigSolveThreads = 128;
+
+template <int F>
+__global__ void __launch_bounds__(kBigSolveThreads) k_solve_big(const float* __restrict__ G_aug,
+                                                               const int32_t* __restrict__ rows, int n_list,
+                                                               Params p, float* __restrict__ X_out,
+                                                               int32_t* __restrict__ flags_out, Counters* cnt,
+                                                               Fallback fb) {
+    extern __shared__ float smem_f[];
+    float (*A)[F + 1] = reinterpret_cast<float (*)[F + 1]>(smem_f);
+    __shared__ int s_piv;
+    __shared__ float s_x[F];
+    const int tid = threadIdx.x;
+    const int w = blockIdx.x;
+    if (w >= n_list) return;
+    const float* src = G_aug + (int64_t)w * F * (F + 1);
+    for (int e = tid; e < F * (F + 1); e += kBigSolveThreads) (&A[0][0])[e] = src[e];
+    __syncthreads();
+    float ratio;
+    const int flags = cta_lu_solve<float, F>(A, s_x, &s_piv, p.f, p.gram_mode == GRAM_ASYM, p.ratio_max, ratio);
     const int64_t i = rows ? (int64_t)rows[w] : (int64_t)w;
-    for (int a = tid; a < f; a += kBigSolveThreads) X_out[i * f + a] = singular ? 0.f : s_x[a];
+    const bool singular = flags & FLAG_SINGULAR;
+    for (int a = tid; a < p.f; a += kBigSolveThreads) X_out[i * p.f + a] = singular ? 0.f : s_x[a];
     if (tid == 0) {
         if (flags_out) flags_out[i] = flags;
         record_flags(cnt, flags, ratio);
+        fallback_push(fb, flags, i);
     }
 }
 

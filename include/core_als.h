@@ -219,7 +219,9 @@ int als_sweep(als_handle* h, const als_csr* R_users, const als_csr* R_items, flo
 
 /* Algorithm 2: `sweeps` sweeps starting from M (in: M^(0), out: result);
  * U is output only. If test entries are given (n_test > 0) the report gets
- * the test RMSE after the last sweep. rep_host nullable. */
+ * the test RMSE after the last sweep. rep_host nullable. On a created
+ * stream, after the first sweep the remaining sweeps replay a CUDA graph of
+ * one sweep (captured on the first call with these buffers). */
 int als_fit(als_handle* h, const als_csr* R_users, const als_csr* R_items, int sweeps,
             float* U, float* M, int64_t n_test, const int32_t* test_u, const int32_t* test_m,
             const float* test_r, als_report* rep_host);
@@ -233,6 +235,37 @@ int als_fit_host(als_handle* h, int64_t n_u, int64_t n_m, int64_t nnz,
                  const int32_t* item_indices_host, const float* item_values_host, int sweeps,
                  float* U_host, float* M_host, int64_t n_test, const int32_t* test_u_host,
                  const int32_t* test_m_host, const float* test_r_host, als_report* rep_host);
+
+/* ---------------------------------------------------------------------------
+ * Batches of independent completion problems.
+ *
+ * Problems with the same n_f are concatenated block-diagonally on the device
+ * (user and item indices shifted by each problem's offsets), so one set of
+ * launches per half-sweep serves every problem of that width; rows never
+ * interact, so each problem's result equals the one it gets alone. One
+ * sweep of all groups is captured into a CUDA graph and replayed. Options
+ * other than n_f come from opt; cuda_stream must not be the legacy default
+ * stream (graph capture needs a created stream). */
+typedef struct als_problem {
+    als_csr users;  /* R in CSR (device arrays) */
+    als_csr items;  /* R^T in CSR (device arrays) */
+    int n_f;
+    float* U;       /* device, users.n_rows x n_f: output */
+    float* M;       /* device, items.n_rows x n_f: in M^(0), out result */
+} als_problem;
+
+typedef struct als_batch als_batch;
+
+/* Build the groups, their row plans and the captured sweep (synchronises).
+ * The problems' arrays must stay valid until als_batch_destroy. */
+int als_batch_create(als_batch** batch_host, const als_options* opt_host, int n_problems,
+                     const als_problem* problems_host, void* cuda_stream);
+/* `sweeps` sweeps of Algorithm 2 for every problem from its M (read at the
+ * start), writing U and M back. Enqueued on the batch stream. */
+int als_batch_fit(als_batch* b, int sweeps);
+/* Kernel launches in one replayed sweep (all groups). */
+int64_t als_batch_launches_per_sweep(const als_batch* b);
+int als_batch_destroy(als_batch* b);
 
 /* Bytes of device workspace the handle currently holds. */
 int64_t als_workspace_bytes(const als_handle* h);

@@ -48,6 +48,10 @@ class als_report(C.Structure):
                 ("test_rmse", C.c_double), ("objective", C.c_double), ("sweeps_done", C.c_int)]
 
 
+class als_problem(C.Structure):
+    _fields_ = [("users", als_csr), ("items", als_csr), ("n_f", C.c_int), ("U", C.c_void_p), ("M", C.c_void_p)]
+
+
 # Every symbol the header declares, with (restype, argtypes).
 _P = C.c_void_p
 _I64 = C.c_int64
@@ -72,6 +76,10 @@ SIGNATURES = {
     "als_fit": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, _I64, _P, _P, _P, _P]),
     "als_fit_host": (C.c_int, [_P, _I64, _I64, _I64, _P, _P, _P, _P, _P, _P, C.c_int, _P, _P, _I64, _P, _P,
                                _P, _P]),
+    "als_batch_create": (C.c_int, [_P, _P, C.c_int, _P, _P]),
+    "als_batch_fit": (C.c_int, [_P, C.c_int]),
+    "als_batch_launches_per_sweep": (_I64, [_P]),
+    "als_batch_destroy": (C.c_int, [_P]),
     "als_workspace_bytes": (_I64, [_P]),
     "als_launch_count": (_I64, [_P]),
     "als_status_string": (C.c_char_p, [C.c_int]),

@@ -210,3 +210,58 @@ class CoreALS:
                    int(sweeps), U.ctypes.data_as(C.c_void_p), M.ctypes.data_as(C.c_void_p), n_test, *tp,
                    C.byref(rep))
         return U, M, {k: getattr(rep, k) for k, _ in B.als_report._fields_}
+
+
+class CoreBatch:
+    """Independent completion problems fitted together (als_batch_*).
+
+    problems: list of (DeviceCSR users, DeviceCSR items, n_f, U, M) with U, M
+    device tensors (M holds M^(0) and receives the result). Options other
+    than n_f are shared. The stream is a new CUDA stream unless given.
+    """
+
+    def __init__(self, problems, lam: float, budget: float, gram_mode: str = "asym", reg_mode: str = "weighted",
+                 precision: int = B.ALS_FP32, fp64_fallback: bool = True, refine_steps: int = 0, stream=None):
+        _require_cuda()
+        self.lib = B.load()
+        opt = B.als_options()
+        self.lib.als_default_options(C.byref(opt))
+        opt.lambda_ = float(lam)
+        opt.budget = float(budget)
+        opt.reg_mode = REG_MODES[reg_mode]
+        opt.gram_mode = GRAM_MODES[gram_mode]
+        opt.precision = int(precision)
+        opt.fp64_fallback = 1 if fp64_fallback else 0
+        opt.refine_steps = int(refine_steps)
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.problems = problems  # keep the tensors alive
+        arr = (B.als_problem * len(problems))()
+        for q, (Ru, Ri, n_f, U, M) in enumerate(problems):
+            arr[q] = B.als_problem(Ru.c_struct(), Ri.c_struct(), int(n_f), U.data_ptr(), M.data_ptr())
+        b = C.c_void_p()
+        torch.cuda.current_stream().synchronize()
+        B.check(self.lib.als_batch_create(C.byref(b), C.byref(opt), len(problems), arr,
+                                          C.c_void_p(self.stream.cuda_stream)))
+        self.b = b
+
+    @property
+    def launches_per_sweep(self) -> int:
+        return int(self.lib.als_batch_launches_per_sweep(self.b))
+
+    def fit(self, sweeps: int):
+        B.check(self.lib.als_batch_fit(self.b, int(sweeps)))
+        return self
+
+    def synchronize(self):
+        self.stream.synchronize()
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.als_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -112,6 +112,15 @@ struct als_handle {
     std::vector<cudaEvent_t> event_pool;
     const char* pending_family = nullptr;
     cudaEvent_t pending_start = nullptr;
+    // Captured sweep of als_fit (one cached graph, keyed by its buffers).
+    struct {
+        const int64_t* ru = nullptr;
+        const int64_t* ri = nullptr;
+        float* U = nullptr;
+        float* M = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        int64_t launches = 0;
+    } fit_graph;
 };
 
 namespace {
@@ -357,6 +366,10 @@ int build_plan(als_handle* h, const als_csr* R, Plan** out) {
     if (h->plans.size() >= 8) {
         free_plan(h->plans.front());
         h->plans.erase(h->plans.begin());
+        if (h->fit_graph.exec) {  // it may use the evicted plan
+            cudaGraphExecDestroy(h->fit_graph.exec);
+            h->fit_graph = {};
+        }
     }
     h->plans.push_back(p);
     *out = &h->plans.back();
@@ -669,6 +682,7 @@ int als_destroy(als_handle* h) {
         cudaEventDestroy(t.stop);
     }
     for (auto e : h->event_pool) cudaEventDestroy(e);
+    if (h->fit_graph.exec) cudaGraphExecDestroy(h->fit_graph.exec);
     for (DevBuf* b : {&h->g_aug, &h->misc, &h->host_in, &h->masks, &h->fb_list, &h->delta})
         if (b->p) cudaFree(b->p);
     delete h;
@@ -814,6 +828,31 @@ int als_sweep(als_handle* h, const als_csr* Ru, const als_csr* Ri, float* U, flo
     return als_half_sweep(h, Ri, U, M, nullptr);
 }
 
+// Capture one sweep (users, then items) on the handle's stream into an
+// executable graph. Every buffer and plan it touches must already exist.
+static int capture_sweep(als_handle* h, const als_csr* Ru, const als_csr* Ri, float* U, float* M,
+                         cudaGraphExec_t* exec, int64_t* launches) {
+    const bool prof = h->profiling;
+    h->profiling = false;
+    const int64_t before = h->launches;
+    ALS_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = als_sweep(h, Ru, Ri, U, M);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    h->profiling = prof;
+    *launches = h->launches - before;
+    h->launches = before;
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return set_err(h, ALS_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return set_err(h, ALS_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    return ALS_OK;
+}
+
 int als_fit(als_handle* h, const als_csr* Ru, const als_csr* Ri, int sweeps, float* U, float* M, int64_t n_test,
             const int32_t* tu, const int32_t* tm, const float* tr, als_report* rep) {
     if (!h) return ALS_ERR_ARG;
@@ -821,7 +860,33 @@ int als_fit(als_handle* h, const als_csr* Ru, const als_csr* Ri, int sweeps, flo
     if (!Ru || !Ri) return set_err(h, ALS_ERR_ARG, "null rating structure");
     if (Ru->n_rows != Ri->n_cols || Ru->n_cols != Ri->n_rows || Ru->nnz != Ri->nnz)
         return set_err(h, ALS_ERR_ARG, "user and item sides do not describe the same matrix");
-    for (int t = 0; t < sweeps; ++t) {
+    // First sweep directly (it builds plans and workspace), the rest from a
+    // captured graph when the stream allows capture and profiling is off.
+    const bool use_graph = sweeps >= 2 && h->stream != nullptr && !h->profiling;
+    int done = 0;
+    if (sweeps > 0) {
+        int rc = als_sweep(h, Ru, Ri, U, M);
+        if (rc) return rc;
+        done = 1;
+    }
+    if (use_graph) {
+        auto& g = h->fit_graph;
+        if (!(g.exec && g.ru == Ru->indptr && g.ri == Ri->indptr && g.U == U && g.M == M)) {
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+            int rc = capture_sweep(h, Ru, Ri, U, M, &g.exec, &g.launches);
+            if (rc) return rc;
+            g.ru = Ru->indptr;
+            g.ri = Ri->indptr;
+            g.U = U;
+            g.M = M;
+        }
+        for (; done < sweeps; ++done) {
+            ALS_CUDA(h, cudaGraphLaunch(g.exec, h->stream));
+            h->launches += g.launches;
+        }
+    }
+    for (; done < sweeps; ++done) {
         int rc = als_sweep(h, Ru, Ri, U, M);
         if (rc) return rc;
     }
@@ -890,7 +955,12 @@ int als_fit_host(als_handle* h, int64_t n_u, int64_t n_m, int64_t nnz, const int
     ALS_CUDA(h, cudaMemcpyAsync(M_host, d_M, n_m * f * 4, cudaMemcpyDeviceToHost, st));
     ALS_CUDA(h, cudaStreamSynchronize(st));
     // The device copies of the structure are reused by later calls only if
-    // they hold the same data, which this call cannot know: drop their plans.
+    // they hold the same data, which this call cannot know: drop their plans
+    // and the captured sweep.
+    if (h->fit_graph.exec) {
+        cudaGraphExecDestroy(h->fit_graph.exec);
+        h->fit_graph = {};
+    }
     h->plans.erase(std::remove_if(h->plans.begin(), h->plans.end(),
                                   [&](const Plan& p) {
                                       bool mine = p.indptr == d_uip || p.indptr == d_iip;
@@ -984,3 +1054,196 @@ extern "C" int als_eval_sse_static(int64_t n, const int32_t* iu, const int32_t* 
     als::k_sum_partials<<<1, 32, 0, st>>>(partials, blocks, sse_dev);
     return cudaGetLastError() == cudaSuccess ? ALS_OK : ALS_ERR_CUDA;
 }
+
+// ---------------------------------------------------------------------------
+// Batches of independent problems (als_batch_*).
+namespace {
+
+// dst[e] = src[e] + add for e < n.
+__global__ void k_shift_i64(int64_t* __restrict__ dst, const int64_t* __restrict__ src, int64_t n, int64_t add) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        dst[e] = src[e] + add;
+}
+__global__ void k_shift_i32(int32_t* __restrict__ dst, const int32_t* __restrict__ src, int64_t n, int32_t add) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        dst[e] = src[e] + add;
+}
+
+struct BatchGroup {
+    int n_f = 0;
+    als_handle* h = nullptr;
+    void* mem = nullptr;
+    als_csr users{}, items{};
+    float* U = nullptr;
+    float* M = nullptr;
+    std::vector<int> members;
+    std::vector<int64_t> u_off, m_off;
+};
+
+}  // namespace
+
+struct als_batch {
+    cudaStream_t stream = nullptr;
+    std::vector<als_problem> probs;
+    std::vector<BatchGroup> groups;
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches = 0;
+};
+
+static void batch_free(als_batch* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (auto& g : b->groups) {
+        if (g.h) als_destroy(g.h);
+        if (g.mem) cudaFree(g.mem);
+    }
+    delete b;
+}
+
+extern "C" int als_batch_create(als_batch** out, const als_options* opt, int n, const als_problem* probs,
+                                void* stream) {
+    if (!out || !opt || n <= 0 || !probs) return ALS_ERR_ARG;
+    *out = nullptr;
+    if (stream == nullptr) return ALS_ERR_ARG;  // capture needs a created stream
+    als_batch* b = new als_batch();
+    b->stream = reinterpret_cast<cudaStream_t>(stream);
+    b->probs.assign(probs, probs + n);
+    for (int q = 0; q < n; ++q) {
+        const als_problem& pr = probs[q];
+        if (pr.users.n_rows != pr.items.n_cols || pr.users.n_cols != pr.items.n_rows || pr.users.nnz != pr.items.nnz ||
+            !pr.U || !pr.M || pr.n_f < 1) {
+            batch_free(b);
+            return ALS_ERR_ARG;
+        }
+        auto it = std::find_if(b->groups.begin(), b->groups.end(), [&](const BatchGroup& g) { return g.n_f == pr.n_f; });
+        if (it == b->groups.end()) {
+            b->groups.emplace_back();
+            b->groups.back().n_f = pr.n_f;
+            it = b->groups.end() - 1;
+        }
+        it->members.push_back(q);
+    }
+    int rc = ALS_OK;
+    for (auto& g : b->groups) {
+        // Offsets and sizes of the block-diagonal concatenation.
+        int64_t nu = 0, nm = 0, nnz = 0;
+        for (int q : g.members) {
+            g.u_off.push_back(nu);
+            g.m_off.push_back(nm);
+            nu += probs[q].users.n_rows;
+            nm += probs[q].items.n_rows;
+            nnz += probs[q].users.nnz;
+        }
+        if (nu > 0x7fffffff || nm > 0x7fffffff) {
+            rc = ALS_ERR_ARG;
+            break;
+        }
+        auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+        const size_t s_up = al((nu + 1) * 8), s_ip = al((nm + 1) * 8), s_ix = al(nnz * 4), s_v = al(nnz * 4);
+        const size_t s_U = al(nu * g.n_f * 4), s_M = al(nm * g.n_f * 4);
+        if (cudaMalloc(&g.mem, s_up + s_ip + 2 * s_ix + 2 * s_v + s_U + s_M) != cudaSuccess) {
+            cudaGetLastError();
+            rc = ALS_ERR_OOM;
+            break;
+        }
+        char* base = reinterpret_cast<char*>(g.mem);
+        int64_t* up = reinterpret_cast<int64_t*>(base);
+        int64_t* ip = reinterpret_cast<int64_t*>(base + s_up);
+        int32_t* ux = reinterpret_cast<int32_t*>(base + s_up + s_ip);
+        int32_t* ix = reinterpret_cast<int32_t*>(base + s_up + s_ip + s_ix);
+        float* uv = reinterpret_cast<float*>(base + s_up + s_ip + 2 * s_ix);
+        float* iv = reinterpret_cast<float*>(base + s_up + s_ip + 2 * s_ix + s_v);
+        g.U = reinterpret_cast<float*>(base + s_up + s_ip + 2 * s_ix + 2 * s_v);
+        g.M = reinterpret_cast<float*>(base + s_up + s_ip + 2 * s_ix + 2 * s_v + s_U);
+        int64_t eo = 0;
+        for (size_t k = 0; k < g.members.size() && rc == ALS_OK; ++k) {
+            const als_problem& pr = probs[g.members[k]];
+            const int64_t uo = g.u_off[k], mo = g.m_off[k], e = pr.users.nnz;
+            k_shift_i64<<<256, 256, 0, b->stream>>>(up + uo, pr.users.indptr, pr.users.n_rows + 1, eo);
+            k_shift_i64<<<256, 256, 0, b->stream>>>(ip + mo, pr.items.indptr, pr.items.n_rows + 1, eo);
+            if (e > 0) {
+                k_shift_i32<<<1024, 256, 0, b->stream>>>(ux + eo, pr.users.indices, e, (int32_t)mo);
+                k_shift_i32<<<1024, 256, 0, b->stream>>>(ix + eo, pr.items.indices, e, (int32_t)uo);
+                cudaMemcpyAsync(uv + eo, pr.users.values, e * 4, cudaMemcpyDeviceToDevice, b->stream);
+                cudaMemcpyAsync(iv + eo, pr.items.values, e * 4, cudaMemcpyDeviceToDevice, b->stream);
+            }
+            if (cudaGetLastError() != cudaSuccess) rc = ALS_ERR_CUDA;
+            eo += e;
+        }
+        if (rc) break;
+        cudaMemsetAsync(g.M, 0, s_M, b->stream);
+        g.users = als_csr{nu, nm, nnz, up, ux, uv};
+        g.items = als_csr{nm, nu, nnz, ip, ix, iv};
+        als_options o = *opt;
+        o.n_f = g.n_f;
+        rc = als_create(&g.h, &o, stream);
+        if (rc) break;
+        // One direct sweep builds the plans (validation included) and workspace.
+        rc = als_prepare(g.h, &g.users);
+        if (!rc) rc = als_prepare(g.h, &g.items);
+        if (!rc) rc = als_sweep(g.h, &g.users, &g.items, g.U, g.M);
+        if (rc) break;
+    }
+    if (rc == ALS_OK) {
+        // Capture one sweep of every group.
+        if (cudaStreamSynchronize(b->stream) != cudaSuccess ||
+            cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            rc = ALS_ERR_CUDA;
+        } else {
+            for (auto& g : b->groups) {
+                const int64_t before = g.h->launches;
+                int r2 = als_sweep(g.h, &g.users, &g.items, g.U, g.M);
+                b->launches += g.h->launches - before;
+                g.h->launches = before;
+                if (r2 && rc == ALS_OK) rc = r2;
+            }
+            cudaGraph_t graph = nullptr;
+            if (cudaStreamEndCapture(b->stream, &graph) != cudaSuccess && rc == ALS_OK) rc = ALS_ERR_CUDA;
+            if (rc == ALS_OK && cudaGraphInstantiate(&b->exec, graph, 0) != cudaSuccess) rc = ALS_ERR_CUDA;
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+        }
+    }
+    if (rc) {
+        batch_free(b);
+        return rc;
+    }
+    *out = b;
+    return ALS_OK;
+}
+
+extern "C" int als_batch_fit(als_batch* b, int sweeps) {
+    if (!b || sweeps < 0) return ALS_ERR_ARG;
+    cudaStream_t st = b->stream;
+    for (auto& g : b->groups)
+        for (size_t k = 0; k < g.members.size(); ++k) {
+            const als_problem& pr = b->probs[g.members[k]];
+            if (cudaMemcpyAsync(g.M + g.m_off[k] * g.n_f, pr.M, pr.items.n_rows * g.n_f * 4, cudaMemcpyDeviceToDevice,
+                                st) != cudaSuccess)
+                return ALS_ERR_CUDA;
+        }
+    for (int t = 0; t < sweeps; ++t) {
+        if (cudaGraphLaunch(b->exec, st) != cudaSuccess) return ALS_ERR_CUDA;
+    }
+    for (auto& g : b->groups)
+        for (size_t k = 0; k < g.members.size(); ++k) {
+            const als_problem& pr = b->probs[g.members[k]];
+            if (cudaMemcpyAsync(pr.U, g.U + g.u_off[k] * g.n_f, pr.users.n_rows * g.n_f * 4, cudaMemcpyDeviceToDevice,
+                                st) != cudaSuccess ||
+                cudaMemcpyAsync(pr.M, g.M + g.m_off[k] * g.n_f, pr.items.n_rows * g.n_f * 4, cudaMemcpyDeviceToDevice,
+                                st) != cudaSuccess)
+                return ALS_ERR_CUDA;
+        }
+    return ALS_OK;
+}
+
+extern "C" int64_t als_batch_launches_per_sweep(const als_batch* b) { return b ? b->launches : 0; }
+
+extern "C" int als_batch_destroy(als_batch* b) {
+    if (!b) return ALS_ERR_ARG;
+    cudaStreamSynchronize(b->stream);
+    batch_free(b);
+    return ALS_OK;
+}
+

@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--precision", choices=["fp32", "tf32", "bf16", "fp32_tc"], default="fp32")
+    ap.add_argument("--no-autotune", action="store_true")
     return ap.parse_args()
 
 
@@ -169,10 +170,13 @@ def gpu_arm(args, p, w, M0, r, rank, world, local_rank):
     Ri = core_als.DeviceCSR.from_host(p.train_cols, dev)
     tu, tm, tr = (torch.as_tensor(a).to(dev) for a in (p.test_u, p.test_m, p.test_r))
     eng = core_als.CoreALS(f, lam, r, gram_mode="asym", precision=PRECISIONS[args.precision])
-    eng.prepare(Ru)
-    eng.prepare(Ri)
     M = torch.as_tensor(M0).to(dev)
     U = torch.empty((p.n_u, f), dtype=torch.float32, device=dev)
+    tuning = None
+    if not args.no_autotune:
+        tuning = eng.autotune(Ru, Ri, U, M, trials=3)
+    eng.prepare(Ru)
+    eng.prepare(Ri)
     sse = torch.zeros(1, dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
@@ -231,7 +235,8 @@ def gpu_arm(args, p, w, M0, r, rank, world, local_rank):
            "vs_baseline": None, "dtype": {"fp32": "f32", "fp32_tc": "f32 (split tf32)", "tf32": "tf32/f32",
                                           "bf16": "bf16/f32"}[args.precision], "data": "synthetic (seeded Zipf rating matrix; no dataset)",
            "config": dict(workload_config(w, r), l2="flushed between steps (256 MB write)",
-                          parallelism="replicas" if world > 1 else "single GPU"),
+                          parallelism="replicas" if world > 1 else "single GPU", precision=args.precision,
+                          schedule=tuning if tuning else "default (not autotuned)"),
            "gpu_launches": launches, "roofline": roof, "clocks": clk.summary(),
            "kernels_ms_per_step": {k: v[0] / args.steps for k, v in fam.items()},
            "test_rmse_after_timed_sweeps": test_rmse}

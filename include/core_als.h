@@ -237,6 +237,36 @@ int als_fit_host(als_handle* h, int64_t n_u, int64_t n_m, int64_t nnz,
                  const int32_t* test_m_host, const float* test_r_host, als_report* rep_host);
 
 /* ---------------------------------------------------------------------------
+ * Autotuning of the row schedule on the live problem.
+ *
+ *   split_at_middle  1: rows longer than the middle CTA capacity take the
+ *                    split (multi-CTA) path; 0: only rows longer than the
+ *                    largest capacity do.
+ *   warp_rows        1: rows with <= 32 observations (n_f <= 32) use the
+ *                    fused warp-per-row kernel; 0: the CTA kernel.
+ *   tc_gram          ALS_FP32 at n_f <= 32 only - 1: assemble with the
+ *                    FP32-accurate split-TF32 tensor-core Gram instead of
+ *                    CUDA cores (both meet the same accuracy).
+ */
+typedef struct als_tuning {
+    int split_at_middle;
+    int warp_rows;
+    int tc_gram;
+    double ms_per_sweep;  /* als_autotune: time of the chosen schedule */
+} als_tuning;
+
+/* Time every candidate schedule over `trials` sweeps (after one warm-up
+ * sweep) on this problem, keep the fastest in the handle and return it. A
+ * process-wide cache keyed by (n_f, precision, log2 histogram of both sides'
+ * row lengths) skips the timing for a problem of the same shape. U and M
+ * are overwritten (M is restored to its value on entry). Synchronises. */
+int als_autotune(als_handle* h, const als_csr* R_users, const als_csr* R_items, float* U, float* M, int trials,
+                 als_tuning* chosen_host);
+/* Set (or read back) the schedule explicitly; plans are rebuilt lazily. */
+int als_set_tuning(als_handle* h, const als_tuning* t_host);
+int als_get_tuning(const als_handle* h, als_tuning* t_host);
+
+/* ---------------------------------------------------------------------------
  * Batches of independent completion problems.
  *
  * Problems with the same n_f are concatenated block-diagonally on the device

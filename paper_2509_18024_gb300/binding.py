@@ -48,6 +48,11 @@ class als_report(C.Structure):
                 ("test_rmse", C.c_double), ("objective", C.c_double), ("sweeps_done", C.c_int)]
 
 
+class als_tuning(C.Structure):
+    _fields_ = [("split_at_middle", C.c_int), ("warp_rows", C.c_int), ("tc_gram", C.c_int),
+                ("ms_per_sweep", C.c_double)]
+
+
 class als_problem(C.Structure):
     _fields_ = [("users", als_csr), ("items", als_csr), ("n_f", C.c_int), ("U", C.c_void_p), ("M", C.c_void_p)]
 
@@ -76,6 +81,9 @@ SIGNATURES = {
     "als_fit": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, _I64, _P, _P, _P, _P]),
     "als_fit_host": (C.c_int, [_P, _I64, _I64, _I64, _P, _P, _P, _P, _P, _P, C.c_int, _P, _P, _I64, _P, _P,
                                _P, _P]),
+    "als_autotune": (C.c_int, [_P, _P, _P, _P, _P, C.c_int, _P]),
+    "als_set_tuning": (C.c_int, [_P, _P]),
+    "als_get_tuning": (C.c_int, [_P, _P]),
     "als_batch_create": (C.c_int, [_P, _P, C.c_int, _P, _P]),
     "als_batch_fit": (C.c_int, [_P, C.c_int]),
     "als_batch_launches_per_sweep": (_I64, [_P]),

@@ -165,6 +165,17 @@ class CoreALS:
         self._call(self.lib.als_kernel_time, family.encode() if family else None, C.byref(ms), C.byref(n))
         return ms.value, n.value
 
+    def autotune(self, Ru: DeviceCSR, Ri: DeviceCSR, U: torch.Tensor, M: torch.Tensor, trials: int = 3) -> dict:
+        """Time the candidate schedules on this problem and keep the fastest."""
+        t = B.als_tuning()
+        self._call(self.lib.als_autotune, C.byref(Ru.c_struct()), C.byref(Ri.c_struct()), B.ptr(U), B.ptr(M),
+                   int(trials), C.byref(t))
+        return {k: getattr(t, k) for k, _ in B.als_tuning._fields_}
+
+    def set_tuning(self, split_at_middle=0, warp_rows=1, tc_gram=0):
+        t = B.als_tuning(int(split_at_middle), int(warp_rows), int(tc_gram), 0.0)
+        self._call(self.lib.als_set_tuning, C.byref(t))
+
     def report(self) -> dict:
         rep = B.als_report()
         self._call(self.lib.als_get_report, C.byref(rep))

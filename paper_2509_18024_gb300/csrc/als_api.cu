@@ -35,6 +35,7 @@ BucketCaps bucket_caps(int F) {
 }
 
 struct Plan {
+    als_tuning tuning{};
     const int64_t* indptr = nullptr;
     int64_t n_rows = 0, nnz = 0, n_cols = 0;
     int F = 0;
@@ -93,6 +94,7 @@ struct als_handle {
     cudaStream_t stream = nullptr;
     int device = 0;
     std::vector<Plan> plans;
+    als_tuning tuning{0, 1, 0, 0.0};
     DevBuf g_aug;     // augmented systems of CTA rows
     DevBuf misc;      // counters + eval partials + error word
     DevBuf host_in;   // device copies for als_fit_host
@@ -211,6 +213,9 @@ int padded_width(int f, int precision) {
     return F <= 128 ? F : 0;
 }
 
+// Padded width the plans and kernels of a handle use (its options and tuning).
+int plan_width(const ::als_handle* h);
+
 // Gram engine for an option set: FP32 runs on CUDA cores up to 32 features
 // and as split TF32 on tensor cores above; the other precisions always use
 // tensor cores.
@@ -262,6 +267,11 @@ int check_csr(als_handle* h, const als_csr* R) {
 }
 
 Counters* counters(als_handle* h) { return reinterpret_cast<Counters*>(h->misc.p); }
+
+int plan_width(const als_handle* h) {
+    const int F = padded_width(h->opt.n_f, h->opt.precision);
+    return (h->tuning.tc_gram && h->opt.precision == ALS_FP32 && F <= 32) ? 32 : F;
+}
 // Counters of the refinement's second solve (not reported).
 Counters* scratch_counters(als_handle* h) { return reinterpret_cast<Counters*>(reinterpret_cast<char*>(h->misc.p) + 128); }
 double* eval_partials(als_handle* h) {
@@ -273,7 +283,9 @@ constexpr size_t kMiscBytes = 256 + (als::kEvalBlocks + 1) * sizeof(double) + 64
 
 int build_plan(als_handle* h, const als_csr* R, Plan** out) {
     for (auto& p : h->plans) {
-        if (p.indptr == R->indptr && p.n_rows == R->n_rows && p.nnz == R->nnz && p.n_cols == R->n_cols) {
+        if (p.indptr == R->indptr && p.n_rows == R->n_rows && p.nnz == R->nnz && p.n_cols == R->n_cols &&
+            p.tuning.split_at_middle == h->tuning.split_at_middle && p.tuning.warp_rows == h->tuning.warp_rows &&
+            p.tuning.tc_gram == h->tuning.tc_gram) {
             *out = &p;
             return ALS_OK;
         }
@@ -296,7 +308,7 @@ int build_plan(als_handle* h, const als_csr* R, Plan** out) {
     if (err & 2u) return set_err(h, ALS_ERR_CSR, "indices out of range, unsorted or duplicated inside a row");
     if (err & 4u) return set_err(h, ALS_ERR_NONFINITE, "non-finite rating value");
 
-    const int F = padded_width(h->opt.n_f, h->opt.precision);
+    const int F = plan_width(h);
     const BucketCaps caps = bucket_caps(F);
     const int chunk = als::split_chunk(F);
     std::vector<int32_t> warp_rows, bucket[3], split_rows;
@@ -304,10 +316,11 @@ int build_plan(als_handle* h, const als_csr* R, Plan** out) {
     for (int64_t i = 0; i < R->n_rows; ++i) {
         const int64_t len = indptr[i + 1] - indptr[i];
         max_len = std::max(max_len, len);
-        if (len <= als::kWarpRowMax && F <= 32) warp_rows.push_back((int32_t)i);
+        const int top = h->tuning.split_at_middle ? caps.cap[1] : caps.cap[2];
+        if (len <= als::kWarpRowMax && F <= 32 && h->tuning.warp_rows) warp_rows.push_back((int32_t)i);
         else if (len <= caps.cap[0]) bucket[0].push_back((int32_t)i);
         else if (len <= caps.cap[1]) bucket[1].push_back((int32_t)i);
-        else if (len <= caps.cap[2]) bucket[2].push_back((int32_t)i);
+        else if (len <= top) bucket[2].push_back((int32_t)i);
         else split_rows.push_back((int32_t)i);
     }
     auto longer = [&](int32_t a, int32_t b) { return indptr[a + 1] - indptr[a] > indptr[b + 1] - indptr[b]; };
@@ -332,6 +345,7 @@ int build_plan(als_handle* h, const als_csr* R, Plan** out) {
     p.nnz = R->nnz;
     p.n_cols = R->n_cols;
     p.F = F;
+    p.tuning = h->tuning;
     p.n_warp = (int)warp_rows.size();
     for (int q = 0; q < 3; ++q) p.n_bucket[q] = (int)bucket[q].size();
     p.n_slots = (int)split_rows.size();
@@ -571,8 +585,12 @@ int run_side(als_handle* h, const Plan& pl, const Side& side, int mode, float* X
 // All built (width, engine) pairs.
 int run_side_any(als_handle* h, const Plan& pl, const Side& side, int mode, float* X_out, int32_t* flags_out,
                  uint32_t* masks_out, float* G_out, float* b_out) {
-    const int F = padded_width(h->opt.n_f, h->opt.precision);
-    const int eng = engine_of(h->opt.precision, F);
+    int F = padded_width(h->opt.n_f, h->opt.precision);
+    int eng = engine_of(h->opt.precision, F);
+    if (h->tuning.tc_gram && h->opt.precision == ALS_FP32 && F <= 32) {
+        F = 32;  // the tensor-core tiles start at 32 features
+        eng = als::ENG_TF32X3;
+    }
 #define ALS_RUN(FF, EE)                                                                          \
     if (F == FF && eng == EE) return run_side<FF, EE>(h, pl, side, mode, X_out, flags_out, masks_out, G_out, b_out)
     ALS_RUN(8, als::ENG_CUDA);
@@ -1053,6 +1071,130 @@ extern "C" int als_eval_sse_static(int64_t n, const int32_t* iu, const int32_t* 
     als::k_sse<<<blocks, als::kEvalThreads, 0, st>>>(n, iu, im, r, U, M, n_f, partials);
     als::k_sum_partials<<<1, 32, 0, st>>>(partials, blocks, sse_dev);
     return cudaGetLastError() == cudaSuccess ? ALS_OK : ALS_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner (als_autotune).
+#include <map>
+#include <mutex>
+
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::vector<int64_t>, als_tuning> g_tune_cache;
+
+// (n_f, precision, log2 length histogram of both sides) of a problem.
+int tune_key(als_handle* h, const als_csr* Ru, const als_csr* Ri, std::vector<int64_t>* key) {
+    key->assign({h->opt.n_f, h->opt.precision, h->opt.gram_mode});
+    for (const als_csr* R : {Ru, Ri}) {
+        std::vector<int64_t> ip(R->n_rows + 1);
+        ALS_CUDA(h, cudaMemcpy(ip.data(), R->indptr, ip.size() * 8, cudaMemcpyDeviceToHost));
+        int64_t hist[40] = {0};
+        for (int64_t i = 0; i < R->n_rows; ++i) {
+            const int64_t len = ip[i + 1] - ip[i];
+            int b = 0;
+            while (b < 39 && (int64_t(1) << b) <= len) ++b;
+            hist[b]++;
+        }
+        key->insert(key->end(), hist, hist + 40);
+    }
+    return ALS_OK;
+}
+
+}  // namespace
+
+extern "C" int als_set_tuning(als_handle* h, const als_tuning* t) {
+    if (!h || !t) return ALS_ERR_ARG;
+    h->tuning = *t;
+    h->tuning.split_at_middle = t->split_at_middle ? 1 : 0;
+    h->tuning.warp_rows = t->warp_rows ? 1 : 0;
+    h->tuning.tc_gram = t->tc_gram ? 1 : 0;
+    if (h->fit_graph.exec) {
+        cudaGraphExecDestroy(h->fit_graph.exec);
+        h->fit_graph = {};
+    }
+    return ALS_OK;
+}
+
+extern "C" int als_get_tuning(const als_handle* h, als_tuning* t) {
+    if (!h || !t) return ALS_ERR_ARG;
+    *t = h->tuning;
+    return ALS_OK;
+}
+
+extern "C" int als_autotune(als_handle* h, const als_csr* Ru, const als_csr* Ri, float* U, float* M, int trials,
+                            als_tuning* chosen) {
+    if (!h || !Ru || !Ri || !U || !M || trials < 1) return ALS_ERR_ARG;
+    std::vector<int64_t> key;
+    int rc = tune_key(h, Ru, Ri, &key);
+    if (rc) return rc;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            rc = als_set_tuning(h, &it->second);
+            if (!rc && chosen) *chosen = it->second;
+            return rc;
+        }
+    }
+    const bool fp32_small = h->opt.precision == ALS_FP32 && h->opt.n_f <= 32;
+    std::vector<als_tuning> cands;
+    for (int split = 0; split < 2; ++split)
+        for (int warp = 0; warp < 2; ++warp)
+            for (int tc = 0; tc < (fp32_small ? 2 : 1); ++tc) {
+                if (!warp && h->opt.n_f > 32) continue;
+                cands.push_back(als_tuning{split, warp, tc, 0.0});
+            }
+    // Keep M^(0): every trial starts from it.
+    float* M0 = nullptr;
+    const size_t mbytes = (size_t)Ri->n_rows * h->opt.n_f * sizeof(float);
+    if (cudaMalloc(&M0, std::max<size_t>(mbytes, 4)) != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(h, ALS_ERR_OOM, "autotune: no memory for M^(0)");
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const als_tuning saved = h->tuning;
+    const bool prof = h->profiling;
+    h->profiling = false;
+    als_tuning best{};
+    double best_ms = 1e300;
+    rc = cudaMemcpyAsync(M0, M, mbytes, cudaMemcpyDeviceToDevice, h->stream) == cudaSuccess ? ALS_OK : ALS_ERR_CUDA;
+    for (size_t c = 0; c < cands.size() && rc == ALS_OK; ++c) {
+        rc = als_set_tuning(h, &cands[c]);
+        if (!rc) rc = als_sweep(h, Ru, Ri, U, M);  // warm-up: plans and workspace
+        if (rc) break;
+        cudaEventRecord(e0, h->stream);
+        for (int t = 0; t < trials && rc == ALS_OK; ++t) rc = als_sweep(h, Ru, Ri, U, M);
+        cudaEventRecord(e1, h->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = ALS_ERR_CUDA;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        cands[c].ms_per_sweep = ms / trials;
+        if (cands[c].ms_per_sweep < best_ms) {
+            best_ms = cands[c].ms_per_sweep;
+            best = cands[c];
+        }
+        if (cudaMemcpyAsync(M, M0, mbytes, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess) rc = ALS_ERR_CUDA;
+    }
+    cudaStreamSynchronize(h->stream);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(M0);
+    h->profiling = prof;
+    if (rc) {
+        als_set_tuning(h, &saved);
+        return rc;
+    }
+    als_set_tuning(h, &best);
+    h->tuning.ms_per_sweep = best_ms;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = h->tuning;
+    }
+    if (chosen) *chosen = h->tuning;
+    return ALS_OK;
 }
 
 // ---------------------------------------------------------------------------

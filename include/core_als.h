@@ -297,6 +297,34 @@ int als_batch_fit(als_batch* b, int sweeps);
 int64_t als_batch_launches_per_sweep(const als_batch* b);
 int als_batch_destroy(als_batch* b);
 
+/* ---------------------------------------------------------------------------
+ * Learned warm start (no counterpart in the paper).
+ *
+ * Per-row features of one side from the other side's factor Y:
+ *   feat_i = [ sum_j r_ij y_j / sum_j r_ij  (n_f values),  log(1 + n_i),
+ *              mean_j r_ij ]                         (n_rows x (n_f + 2))
+ * and a 3-layer MLP  y = W3 GELU(W2 GELU(W1 x + b1) + b2) + b3  (GELU with
+ * erf) trained on MSE by Adam (beta 0.9 / 0.999, eps 1e-8). Master weights
+ * are FP32; the forward and backward products use their BF16 rounding;
+ * activations and sums are FP32 and every reduction has a fixed order.
+ * Parameters (FP32, flat): W1 (hidden x in), b1, W2 (hidden x hidden), b2,
+ * W3 (out x hidden), b3. X, Y, T are device arrays, row-major. */
+typedef struct als_mlp als_mlp;
+int als_features(const als_csr* R_side, const float* Y, int n_f, float* feat_out, void* cuda_stream);
+/* Weights uniform in +-1/sqrt(fan_in) from SplitMix64(seed), zero biases. */
+int als_mlp_create(als_mlp** mlp_host, int in_dim, int hidden, int out_dim, uint64_t seed, void* cuda_stream);
+int als_mlp_destroy(als_mlp* m);
+int64_t als_mlp_num_params(const als_mlp* m);
+int als_mlp_set_params(als_mlp* m, const float* params_host);  /* also resets Adam state (synchronises) */
+int als_mlp_get_params(als_mlp* m, float* params_host);        /* synchronises */
+int als_mlp_forward(als_mlp* m, int64_t n, const float* X, float* Y);
+/* Gradient of the mean squared error at the current weights (no update);
+ * grads_host (nullable) gets n_params floats; synchronises. */
+int als_mlp_grad(als_mlp* m, int64_t n, const float* X, const float* T, float* grads_host, double* loss_host);
+/* One Adam step on a batch of n rows; loss_host (nullable) gets the batch
+ * loss before the step (synchronises only when given). */
+int als_mlp_train_step(als_mlp* m, int64_t n, const float* X, const float* T, float lr, double* loss_host);
+
 /* Bytes of device workspace the handle currently holds. */
 int64_t als_workspace_bytes(const als_handle* h);
 

@@ -88,6 +88,15 @@ SIGNATURES = {
     "als_batch_fit": (C.c_int, [_P, C.c_int]),
     "als_batch_launches_per_sweep": (_I64, [_P]),
     "als_batch_destroy": (C.c_int, [_P]),
+    "als_features": (C.c_int, [_P, _P, C.c_int, _P, _P]),
+    "als_mlp_create": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_uint64, _P]),
+    "als_mlp_destroy": (C.c_int, [_P]),
+    "als_mlp_num_params": (_I64, [_P]),
+    "als_mlp_set_params": (C.c_int, [_P, _P]),
+    "als_mlp_get_params": (C.c_int, [_P, _P]),
+    "als_mlp_forward": (C.c_int, [_P, _I64, _P, _P]),
+    "als_mlp_grad": (C.c_int, [_P, _I64, _P, _P, _P, _P]),
+    "als_mlp_train_step": (C.c_int, [_P, _I64, _P, _P, C.c_float, _P]),
     "als_workspace_bytes": (_I64, [_P]),
     "als_launch_count": (_I64, [_P]),
     "als_status_string": (C.c_char_p, [C.c_int]),

@@ -29,23 +29,34 @@ def nvcc() -> str:
 
 
 def build(force: bool = False, verbose: bool = False) -> Path:
-    """Compile csrc/*.cu into one shared library unless it is up to date."""
+    """Compile each csrc/*.cu in parallel and link one shared library, unless
+    the library is newer than every source."""
     OUT_DIR.mkdir(parents=True, exist_ok=True)
     if LIB.exists() and not force:
         newest = max(p.stat().st_mtime for p in _sources())
         if LIB.stat().st_mtime >= newest:
             return LIB
     tus = sorted(CSRC.glob("*.cu"))
+    compile_flags = [f for f in FLAGS if f != "-shared"]
+    procs = []
+    for tu in tus:
+        obj = OUT_DIR / (tu.stem + ".o")
+        cmd = [nvcc(), *ARCH, *compile_flags, "-I", str(INCLUDE), "-I", str(CSRC), "-c", str(tu), "-o", str(obj)]
+        if verbose:
+            cmd.insert(1, "-Xptxas=-v")
+        procs.append((tu, obj, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)))
+    objs = []
+    for tu, obj, pr in procs:
+        out, err = pr.communicate()
+        if pr.returncode != 0:
+            raise RuntimeError(f"nvcc failed on {tu.name}:\n" + out + err)
+        if verbose:
+            print(err)
+        objs.append(str(obj))
     tmp = str(LIB) + ".tmp"
-    cmd = [nvcc(), *ARCH, *FLAGS, "-I", str(INCLUDE), "-I", str(CSRC), "-o", tmp, *map(str, tus)]
-    if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-        print(" ".join(cmd))
-    r = subprocess.run(cmd, capture_output=True, text=True)
+    r = subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:
-        raise RuntimeError("nvcc failed:\n" + r.stdout + r.stderr)
-    if verbose:
-        print(r.stderr)
+        raise RuntimeError("nvcc link failed:\n" + r.stdout + r.stderr)
     os.replace(tmp, LIB)
     return LIB
 

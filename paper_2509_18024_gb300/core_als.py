@@ -276,3 +276,65 @@ class CoreBatch:
             self.close()
         except Exception:
             pass
+
+
+def features(R: DeviceCSR, Y: torch.Tensor, n_f: int) -> torch.Tensor:
+    """Per-row warm-start features of one side (n_rows x (n_f + 2))."""
+    lib = B.load()
+    out = torch.empty((R.n_rows, n_f + 2), dtype=torch.float32, device=Y.device)
+    B.check(lib.als_features(C.byref(R.c_struct()), B.ptr(Y), int(n_f), B.ptr(out),
+                             C.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    return out
+
+
+class MLP:
+    """The warm-start network (als_mlp_*): in -> hidden -> hidden -> out, GELU."""
+
+    def __init__(self, in_dim: int, hidden: int, out_dim: int, seed: int = 0):
+        _require_cuda()
+        self.lib = B.load()
+        self.dims = (in_dim, hidden, out_dim)
+        m = C.c_void_p()
+        B.check(self.lib.als_mlp_create(C.byref(m), int(in_dim), int(hidden), int(out_dim), int(seed),
+                                        C.c_void_p(torch.cuda.current_stream().cuda_stream)))
+        self.m = m
+        self.n_params = int(self.lib.als_mlp_num_params(m))
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(self.n_params, np.float32)
+        B.check(self.lib.als_mlp_get_params(self.m, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def set_params(self, p: np.ndarray):
+        p = np.ascontiguousarray(p, np.float32)
+        B.check(self.lib.als_mlp_set_params(self.m, p.ctypes.data_as(C.c_void_p)))
+
+    def forward(self, X: torch.Tensor) -> torch.Tensor:
+        X = X.contiguous()
+        Y = torch.empty((X.shape[0], self.dims[2]), dtype=torch.float32, device=X.device)
+        B.check(self.lib.als_mlp_forward(self.m, int(X.shape[0]), B.ptr(X), B.ptr(Y)))
+        return Y
+
+    def grad(self, X: torch.Tensor, T: torch.Tensor):
+        g = np.zeros(self.n_params, np.float32)
+        loss = C.c_double()
+        B.check(self.lib.als_mlp_grad(self.m, int(X.shape[0]), B.ptr(X.contiguous()), B.ptr(T.contiguous()),
+                                      g.ctypes.data_as(C.c_void_p), C.byref(loss)))
+        return loss.value, g
+
+    def train_step(self, X: torch.Tensor, T: torch.Tensor, lr: float, want_loss: bool = False):
+        loss = C.c_double()
+        B.check(self.lib.als_mlp_train_step(self.m, int(X.shape[0]), B.ptr(X), B.ptr(T), float(lr),
+                                            C.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    def close(self):
+        if getattr(self, "m", None):
+            self.lib.als_mlp_destroy(self.m)
+            self.m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

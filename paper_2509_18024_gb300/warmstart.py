@@ -1,0 +1,105 @@
+"""Learned warm start for Core-ALS (the paper has no counterpart).
+
+Two networks map a row's features to its factor: the user net reads
+features computed from the item factor, the item net from the user factor.
+They are trained on factors that ALS itself converged to on seeded training
+matrices (inputs from the converged other side, targets the converged rows).
+At use time, from a random M^(0): U_w = user_net(features(R, M^(0))),
+M_w = item_net(features(R^T, U_w)), and ALS starts from M_w. Plain ALS from
+M^(0) is the judge: if the warm start's test RMSE after the first sweep is
+worse, the fit falls back to M^(0).
+
+This module only orchestrates; features, the networks (forward, backward,
+Adam) and ALS run in libcore_als.so.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import core_als
+
+
+@dataclass
+class Pair:
+    users: core_als.MLP
+    items: core_als.MLP
+
+
+def converged_factors(problem, n_f, lam, budget, M0, sweeps, precision=0, gram_mode="asym"):
+    """ALS from M0 for `sweeps` sweeps; returns device (U, M, Ru, Ri)."""
+    Ru = core_als.DeviceCSR.from_host(problem.train_rows)
+    Ri = core_als.DeviceCSR.from_host(problem.train_cols)
+    eng = core_als.CoreALS(n_f, lam, budget, gram_mode=gram_mode, precision=precision)
+    U, M, _ = eng.fit(Ru, Ri, torch.as_tensor(M0).cuda(), sweeps)
+    return U, M, Ru, Ri
+
+
+def train(problems, n_f, lam, budget, sweeps=15, hidden=256, epochs=30, batch=4096, lr=1e-3, seed=0):
+    """Train the user and item nets on ALS-converged factors of `problems`."""
+    from . import synth
+    Xu, Tu, Xm, Tm = [], [], [], []
+    for q, p in enumerate(problems):
+        M0 = synth.init_factor(p.n_m, n_f, 7000 + q)
+        U, M, Ru, Ri = converged_factors(p, n_f, lam, budget, M0, sweeps)
+        Xu.append(core_als.features(Ru, M, n_f))
+        Tu.append(U)
+        Xm.append(core_als.features(Ri, U, n_f))
+        Tm.append(M)
+    nets = Pair(core_als.MLP(n_f + 2, hidden, n_f, seed), core_als.MLP(n_f + 2, hidden, n_f, seed + 1))
+    gen = torch.Generator(device="cuda").manual_seed(seed)
+    history = {"users": [], "items": []}
+    for net, X, T, key in ((nets.users, torch.cat(Xu), torch.cat(Tu), "users"),
+                           (nets.items, torch.cat(Xm), torch.cat(Tm), "items")):
+        n = X.shape[0]
+        for ep in range(epochs):
+            perm = torch.randperm(n, device="cuda", generator=gen)
+            last = None
+            for s in range(0, n, batch):
+                idx = perm[s:s + batch]
+                want = s + batch >= n
+                last = net.train_step(X[idx].contiguous(), T[idx].contiguous(), lr, want_loss=want)
+            history[key].append(last)
+    return nets, history
+
+
+def warm_factor(nets: Pair, Ru, Ri, M0: torch.Tensor, n_f: int):
+    """M_w from a random M^(0): users from M^(0), then items from the users."""
+    Uw = nets.users.forward(core_als.features(Ru, M0, n_f))
+    return nets.items.forward(core_als.features(Ri, Uw, n_f))
+
+
+def judge(nets: Pair, problem, n_f, lam, budget, M0, sweeps, target=None):
+    """Test RMSE per sweep from M^(0) and from the warm start, the chosen start
+    (warm unless its first-sweep RMSE is worse) and the sweeps each needs to
+    reach `target` (default: the plain run's final RMSE x (1 + 1e-3))."""
+    Ru = core_als.DeviceCSR.from_host(problem.train_rows)
+    Ri = core_als.DeviceCSR.from_host(problem.train_cols)
+    test = tuple(torch.as_tensor(a).cuda() for a in (problem.test_u, problem.test_m, problem.test_r))
+    M0d = torch.as_tensor(M0).cuda()
+    Mw = warm_factor(nets, Ru, Ri, M0d, n_f)
+    curves, times = {}, {}
+    for name, start in (("plain", M0d), ("warm", Mw)):
+        eng = core_als.CoreALS(n_f, lam, budget)
+        M = start.clone()
+        U = torch.empty((problem.n_u, n_f), device="cuda")
+        errs, ms = [], []
+        total = 0.0
+        for _ in range(sweeps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            eng.sweep(Ru, Ri, U, M)
+            b.record()
+            torch.cuda.synchronize()
+            total += a.elapsed_time(b)
+            ms.append(total)
+            errs.append(eng.rmse(*test, U, M))
+        curves[name], times[name] = errs, ms
+    if target is None:
+        target = curves["plain"][-1] * (1 + 1e-3)
+    chosen = "warm" if curves["warm"][0] <= curves["plain"][0] else "plain"
+    reach = {k: next((q + 1 for q, e in enumerate(v) if e <= target), None) for k, v in curves.items()}
+    reach_ms = {k: (times[k][reach[k] - 1] if reach[k] else None) for k in curves}
+    return {"target": target, "curves": curves, "chosen": chosen, "sweeps_to_target": reach, "ms_to_target": reach_ms}

@@ -1,0 +1,95 @@
+"""Warm-start kernels against the FP64 reference: features, forward, the
+analytic gradient and one Adam step; training lowers the loss; the warm
+start is judged against plain ALS (gain reported, fallback checked)."""
+import numpy as np
+import pytest
+
+from oracle import mlp as ref
+from paper_2509_18024_gb300 import synth
+from tests.helpers import rel_fro, rows_problem
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def core():
+    from paper_2509_18024_gb300 import core_als
+    return core_als
+
+
+def bf16(a):
+    t = torch.as_tensor(np.asarray(a, np.float32)).to(torch.bfloat16).to(torch.float32)
+    return t.numpy().astype(np.float64)
+
+
+def test_features_match_reference(core):
+    csr, Y = rows_problem([0, 1, 3, 40, 300, 2000], 3000, 16, seed=3, rating_pool=[1.0, 2.0, 3.0, 4.0, 5.0])
+    F = core.features(core.DeviceCSR.from_host(csr), torch.as_tensor(Y).cuda(), 16).cpu().numpy()
+    Fo = ref.features(csr.indptr, csr.indices, csr.values, Y)
+    np.testing.assert_allclose(F, Fo, rtol=2e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("i,h,o,n", [(34, 256, 32, 5000), (10, 64, 8, 300), (130, 256, 128, 9000)])
+def test_forward_and_gradient_match_reference(core, i, h, o, n):
+    rng = np.random.default_rng(i + h)
+    net = core.MLP(i, h, o, seed=5)
+    params = net.params().astype(np.float64)
+    params[np.concatenate([np.zeros(h * i, bool), np.ones(h, bool), np.zeros(h * h, bool), np.ones(h, bool),
+                           np.zeros(o * h, bool), np.ones(o, bool)])] = rng.standard_normal(2 * h + o) * 0.1
+    net.set_params(params)
+    X = rng.standard_normal((n, i)).astype(np.float32)
+    T = rng.standard_normal((n, o)).astype(np.float32)
+    W1, b1, W2, b2, W3, b3 = ref.unpack(params, i, h, o)
+    wq = (bf16(W1), bf16(W2), bf16(W3))  # the products use the BF16 rounding
+    Y = net.forward(torch.as_tensor(X).cuda()).cpu().numpy()
+    Yo, _ = ref.forward(params, X, i, h, o, wq)
+    assert rel_fro(Y, Yo) <= 1e-5
+    loss, g = net.grad(torch.as_tensor(X).cuda(), torch.as_tensor(T).cuda())
+    lo, go = ref.loss_and_grad(params, X, T, i, h, o, wq)
+    assert loss == pytest.approx(lo, rel=1e-5)
+    assert rel_fro(g, go) <= 1e-4
+
+
+def test_adam_step_matches_reference(core):
+    rng = np.random.default_rng(1)
+    i, h, o, n = 12, 32, 6, 700
+    net = core.MLP(i, h, o, seed=2)
+    p0 = net.params().astype(np.float64)
+    X = rng.standard_normal((n, i)).astype(np.float32)
+    T = rng.standard_normal((n, o)).astype(np.float32)
+    _, g = net.grad(torch.as_tensor(X).cuda(), torch.as_tensor(T).cuda())
+    net.train_step(torch.as_tensor(X).cuda(), torch.as_tensor(T).cuda(), 1e-2)
+    p1 = net.params()
+    po, _, _ = ref.adam(p0, g.astype(np.float64), np.zeros_like(p0), np.zeros_like(p0), 1, 1e-2)
+    np.testing.assert_allclose(p1, po, rtol=1e-5, atol=1e-7)
+
+
+def test_training_lowers_loss(core):
+    rng = np.random.default_rng(2)
+    i, h, o, n = 8, 64, 4, 4096
+    X = rng.standard_normal((n, i)).astype(np.float32)
+    A = rng.standard_normal((i, o))
+    T = (np.tanh(X @ A)).astype(np.float32)
+    net = core.MLP(i, h, o, seed=0)
+    Xd, Td = torch.as_tensor(X).cuda(), torch.as_tensor(T).cuda()
+    first = net.train_step(Xd, Td, 3e-3, want_loss=True)
+    for _ in range(300):
+        last = net.train_step(Xd, Td, 3e-3, want_loss=True)
+    assert last < 0.2 * first
+
+
+def test_warm_start_judged_against_plain_als(core):
+    from paper_2509_18024_gb300 import warmstart
+    f, lam, r = 16, 0.05, 0.25
+    train = [synth.zipf_ratings(3000, 1500, f, 60_000, 1.0, 0.5, seed=s) for s in (11, 12, 13)]
+    nets, hist = warmstart.train(train, f, lam, r, sweeps=12, hidden=64, epochs=20, batch=2048)
+    assert hist["users"][-1] < hist["users"][0]
+    held = synth.zipf_ratings(3000, 1500, f, 60_000, 1.0, 0.5, seed=21)
+    M0 = synth.init_factor(held.n_m, f, 99)
+    res = warmstart.judge(nets, held, f, lam, r, M0, sweeps=12)
+    print("warm start:", res["sweeps_to_target"], res["ms_to_target"], res["chosen"],
+          [round(e, 4) for e in res["curves"]["warm"][:4]], [round(e, 4) for e in res["curves"]["plain"][:4]])
+    # The fallback rule keeps the better first sweep.
+    c = res["curves"]
+    assert c[res["chosen"]][0] <= min(c["warm"][0], c["plain"][0]) + 1e-12

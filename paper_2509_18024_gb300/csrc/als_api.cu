@@ -390,15 +390,51 @@ int build_plan(als_handle* h, const als_csr* R, Plan** out) {
     return ALS_OK;
 }
 
+// Launch shape of a kernel that may hold tensor memory: CUDA-core engines
+// get one CTA per work item; tensor-core engines a persistent grid whose
+// shared-memory request is padded so that the CTAs resident on one SM never
+// need more than its 512 TMEM columns (two accumulators each).
+template <class K>
+int tc_launch_shape(als_handle* h, K kernel, size_t smem, int eng, uint32_t tmem_cols, int count, int mode,
+                    size_t* smem_out, int* grid_out) {
+    *smem_out = smem;
+    *grid_out = count;
+    if (eng == als::ENG_CUDA || mode == 2 || count == 0) return ALS_OK;
+    const int limit = std::max(1, (int)(512 / (2 * tmem_cols)));
+    const size_t per_sm = 233472;   // shared memory of one SM
+    const size_t reserved = 1024;   // per-CTA reservation
+    const size_t floor_smem = per_sm / (limit + 1) - reserved + 1;
+    *smem_out = std::max(smem, std::min<size_t>(floor_smem, 232448));
+    ALS_CUDA(h, cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem_out));
+    ALS_CUDA(h, cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared));
+    // Resident CTAs per SM from shared memory, registers and warps.
+    cudaFuncAttributes fa;
+    ALS_CUDA(h, cudaFuncGetAttributes(&fa, kernel));
+    const int occ_smem = (int)(per_sm / (*smem_out + fa.sharedSizeBytes + reserved));
+    const int warps = als::kCtaThreads / 32;
+    const int regs_per_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
+    const int occ_regs = regs_per_warp > 0 ? 65536 / (regs_per_warp * warps) : 8;
+    const int occ = std::max(1, std::min({occ_smem, occ_regs, 64 / warps, limit}));
+    *grid_out = std::min(count, h->n_sm * occ);
+    return ALS_OK;
+}
+
 template <int F, int NS, int ENG>
 int launch_cta_bucket(als_handle* h, const Side& side, const Params& p, const int32_t* list, int count, int mode,
                       float* G_aug, uint32_t* masks_out) {
     if (count == 0) return ALS_OK;
-    const size_t smem = sizeof(als::CtaSmem<F, NS, ENG>);
-    ALS_CUDA(h, cudaFuncSetAttribute(als::k_cta_rows<F, NS, ENG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
-    ALS_LAUNCH(h, "cta_rows", als::k_cta_rows<F, NS, ENG><<<count, als::kCtaThreads, smem, h->stream>>>(
-                                  side, p, list, count, mode, G_aug, masks_out));
+    auto kern = als::k_cta_rows<F, NS, ENG>;
+    size_t smem = sizeof(als::CtaSmem<F, NS, ENG>);
+    ALS_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int grid = count;
+    if constexpr (ENG != als::ENG_CUDA) {
+        int rc = tc_launch_shape(h, kern, smem, ENG, als::TcCfg<F, als::tc_prec(ENG)>::TMEM_COLS, count, mode, &smem,
+                                 &grid);
+        if (rc) return rc;
+    }
+    ALS_LAUNCH(h, "cta_rows", kern<<<grid, als::kCtaThreads, smem, h->stream>>>(side, p, list, count, mode, G_aug,
+                                                                              masks_out));
     return ALS_OK;
 }
 
@@ -440,11 +476,16 @@ int launch_split(als_handle* h, const Plan& pl, const Side& side, const Params& 
     }
     ALS_LAUNCH(h, "split_eqcount", als::k_split_eqcount<F><<<pl.n_chunks, als::kCtaThreads, 0, st>>>(side, p, sp, ss));
     ALS_LAUNCH(h, "split_cut", als::k_split_cut<F><<<(sc * 32 + 255) / 256, 256, 0, st>>>(side, p, sp, ss));
-    const size_t smem = sizeof(als::SplitGramSmem<F, ENG>);
-    ALS_CUDA(h, cudaFuncSetAttribute(als::k_split_gram<F, ENG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
-    ALS_LAUNCH(h, "split_gram", als::k_split_gram<F, ENG><<<pl.n_chunks, als::kCtaThreads, smem, st>>>(
-                                    side, p, sp, ss, mode, masks_out));
+    auto gkern = als::k_split_gram<F, ENG>;
+    size_t smem = sizeof(als::SplitGramSmem<F, ENG>);
+    ALS_CUDA(h, cudaFuncSetAttribute(gkern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int ggrid = pl.n_chunks;
+    if constexpr (ENG != als::ENG_CUDA) {
+        int rc = tc_launch_shape(h, gkern, smem, ENG, als::TcCfg<F, als::tc_prec(ENG)>::TMEM_COLS, pl.n_chunks, mode,
+                                 &smem, &ggrid);
+        if (rc) return rc;
+    }
+    ALS_LAUNCH(h, "split_gram", gkern<<<ggrid, als::kCtaThreads, smem, st>>>(side, p, sp, ss, mode, masks_out));
     if (mode != 2)
         ALS_LAUNCH(h, "split_reduce",
                    als::k_split_reduce<F><<<pl.n_slots, als::kCtaThreads, 0, st>>>(side, p, sp, ss, G_aug));

@@ -33,13 +33,6 @@ struct MaskWords {
     static constexpr int value = (F + 31) / 32;
 };
 
-// Bytes of the Gram scratch (partials or tensor-core tiles) for an engine.
-template <int F, int ENG>
-struct GramScratch {
-    static constexpr int value =
-        ENG == ENG_CUDA ? kCtaWarps * F * (F + 1) * 4 : TcCfg<F, (ENG == ENG_CUDA ? 0 : tc_prec(ENG))>::TILE_BYTES;
-};
-
 // ---------------------------------------------------------------------------
 // Masked Gram of a staged tile, warps split the positions, lanes tile [G|b]:
 // G[a][b] += w_ka x_ka w'_kb x_kb, rhs[a] += w_ka x_ka r_k.
@@ -158,53 +151,51 @@ __device__ __forceinline__ void build_masks(uint32_t (*mask)[MaskWords<F>::value
     }
 }
 
-// Masked Gram of positions [0, cn) of a staged tile. The result (no
-// regulariser) goes to out(a, c, v) for a < F, c <= F, called once per value
-// by some thread. scratch: GramScratch bytes; bar/tmem_slot for tcgen05.
+// Masked Gram of positions [0, cn) of a staged tile on CUDA cores (FP32,
+// n_f <= 32). The result (no regulariser) goes to out(a, c, v) for a < F,
+// c <= F, called once per value by some thread. scratch: per-warp partials.
 template <int F, int ENG, class Out>
-__device__ __forceinline__ void gram_tile(uint8_t* scratch, uint64_t* bar, uint32_t* tmem_slot, const float (*x)[F],
+__device__ __forceinline__ void gram_tile(uint8_t* scratch, uint64_t*, uint32_t*, const float (*x)[F],
                                           const uint32_t (*mask)[MaskWords<F>::value], const float* r, int cn,
                                           bool sym, Out out) {
+    static_assert(ENG == ENG_CUDA && F <= 32, "CUDA-core Gram is built for n_f <= 32");
     const int tid = threadIdx.x, warp = tid >> 5;
-    if constexpr (ENG == ENG_CUDA) {
-        static_assert(F <= 32, "CUDA-core Gram is built for n_f <= 32");
-        float (*Gp)[F][F + 1] = reinterpret_cast<float (*)[F][F + 1]>(scratch);
-        GramAcc<F> g;
-        g.zero();
-        g.add_tile(x, &mask[0][0], r, warp, cn, kCtaWarps, sym);
-        g.store(Gp[warp]);
-        __syncthreads();
-        for (int e = tid; e < F * (F + 1); e += kCtaThreads) {
-            const int a = e / (F + 1), c = e % (F + 1);
-            float v = 0.f;
+    float (*Gp)[F][F + 1] = reinterpret_cast<float (*)[F][F + 1]>(scratch);
+    GramAcc<F> g;
+    g.zero();
+    g.add_tile(x, &mask[0][0], r, warp, cn, kCtaWarps, sym);
+    g.store(Gp[warp]);
+    __syncthreads();
+    for (int e = tid; e < F * (F + 1); e += kCtaThreads) {
+        const int a = e / (F + 1), c = e % (F + 1);
+        float v = 0.f;
 #pragma unroll
-            for (int q = 0; q < kCtaWarps; ++q) v += Gp[q][a][c];
-            out(a, c, v);
-        }
-    } else {
-        constexpr int PREC = tc_prec(ENG);
-        TcCtx ctx;
-        tc_setup<F, PREC>(scratch, bar, tmem_slot, ctx);
-        tc_accumulate<F, PREC, MaskWords<F>::value>(ctx, scratch, bar, x, mask, r, 0, cn, sym, true);
-        tc_store<F, PREC>(ctx, cn <= 0, out);
-        tc_teardown<F, PREC>(ctx);
+        for (int q = 0; q < kCtaWarps; ++q) v += Gp[q][a][c];
+        out(a, c, v);
     }
 }
 
 // ---------------------------------------------------------------------------
 // CTA per row, slice resident in shared memory (n_i <= NS).
+// Bytes of the two tensor-core tile buffers of an engine (16 for CUDA cores).
+template <int F, int ENG>
+struct TileBytes {
+    static constexpr int value = ENG == ENG_CUDA ? 16 : 2 * TcCfg<F, tc_prec(ENG)>::TILE_BYTES;
+};
+
 template <int F, int NS, int ENG>
 struct CtaSmem {
     static constexpr int W = MaskWords<F>::value;
     static constexpr int HIST_BYTES = F * kHist64Row * 4;
-    static constexpr int GRAM_BYTES = GramScratch<F, ENG>::value;
+    static constexpr int GRAM_BYTES = ENG == ENG_CUDA ? kCtaWarps * F * (F + 1) * 4 : 0;
     static constexpr int U_BYTES = HIST_BYTES > GRAM_BYTES ? HIST_BYTES : GRAM_BYTES;
     float x[NS][F];
     float r[NS];
     int32_t idx[NS];
     uint32_t mask[NS][W];
-    __align__(1024) uint8_t u[U_BYTES];  // histograms, then Gram scratch
-    uint64_t bar;
+    __align__(1024) uint8_t u[U_BYTES];  // histograms (then CUDA-core Gram partials)
+    __align__(1024) uint8_t tiles[TileBytes<F, ENG>::value];  // tensor-core operands
+    uint64_t bars[2];
     uint32_t tmem_slot;
     uint32_t P[F];
     uint32_t Mk[F];
@@ -217,7 +208,10 @@ struct CtaSmem {
 };
 
 // mode 0/1: write the augmented system of list entry w to G_aug[w]; mode 2:
-// masks only.
+// masks only. CTAs loop over list entries w = blockIdx.x + k gridDim.x; with
+// a tensor-core engine the grid is persistent, TMEM and tiles are set up
+// once per CTA, and each row's accumulator is read back after the next row
+// has been staged and selected (its MMAs run meanwhile).
 template <int F, int NS, int ENG>
 __global__ void __launch_bounds__(kCtaThreads) k_cta_rows(Side side, Params p, const int32_t* __restrict__ rows,
                                                           int n_list, int mode, float* __restrict__ G_aug,
@@ -227,9 +221,29 @@ __global__ void __launch_bounds__(kCtaThreads) k_cta_rows(Side side, Params p, c
     Smem& S = *reinterpret_cast<Smem*>(smem_raw);
     constexpr int W = Smem::W;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int w = blockIdx.x;
-    if (w >= n_list) return;
     const int f = p.f;
+    constexpr bool TC = ENG != ENG_CUDA;
+    constexpr int PREC = TC ? tc_prec(ENG) : 0;
+    const bool sym = p.gram_mode == GRAM_SYM;
+    TcPipe P;
+    if constexpr (TC) {
+        if (mode != 2 && blockIdx.x < n_list) tc_pipe_setup<F, PREC>(S.tiles, S.bars, &S.tmem_slot, P);
+    }
+    int prev_w = -1, prev_n = 0, prev_acc = 0, iter = 0;
+    auto finish_prev = [&]() {
+        if constexpr (TC) {
+            if (prev_w < 0) return;
+            float* dst = G_aug + (int64_t)prev_w * F * (F + 1);
+            const float reg = row_reg(prev_n, p);
+            tc_pipe_finish<F, PREC>(P, S.bars, prev_acc, prev_n == 0, [&](int a, int c, float v) {
+                if (a == c) v = (a < f) ? v + reg : 1.f;
+                dst[a * (F + 1) + c] = v;
+            });
+            prev_w = -1;
+        }
+    };
+    for (int w = blockIdx.x; w < n_list; w += gridDim.x, ++iter) {
+    __syncthreads();
     const int64_t i = rows[w];
     const int64_t lo = side.indptr[i];
     const int n = (int)(side.indptr[i + 1] - lo);
@@ -350,14 +364,28 @@ __global__ void __launch_bounds__(kCtaThreads) k_cta_rows(Side side, Params p, c
     __syncthreads();
     if (masks_out != nullptr)
         for (int e = tid; e < n * W; e += kCtaThreads) masks_out[lo * W + e] = (&S.mask[0][0])[e];
-    if (mode == 2) return;
-    float* dst = G_aug + (int64_t)w * F * (F + 1);
-    const float reg = row_reg(n, p);
-    gram_tile<F, ENG>(S.u, &S.bar, &S.tmem_slot, S.x, S.mask, S.r, n, p.gram_mode == GRAM_SYM,
-                      [&](int a, int c, float v) {
-                          if (a == c) v = (a < f) ? v + reg : 1.f;
-                          dst[a * (F + 1) + c] = v;
-                      });
+    if (mode == 2) continue;
+    if constexpr (TC) {
+        finish_prev();
+        tc_pipe_row<F, PREC, W>(P, S.tiles, S.bars, S.x, S.mask, S.r, n, sym, iter & 1);
+        prev_w = w;
+        prev_n = n;
+        prev_acc = iter & 1;
+    } else {
+        float* dst = G_aug + (int64_t)w * F * (F + 1);
+        const float reg = row_reg(n, p);
+        gram_tile<F, ENG>(S.u, nullptr, nullptr, S.x, S.mask, S.r, n, sym, [&](int a, int c, float v) {
+            if (a == c) v = (a < f) ? v + reg : 1.f;
+            dst[a * (F + 1) + c] = v;
+        });
+    }
+    }  // rows of this CTA
+    if constexpr (TC) {
+        if (mode != 2 && blockIdx.x < n_list) {
+            finish_prev();
+            tc_pipe_teardown<F, PREC>(P);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -559,12 +587,14 @@ struct SplitGramSmem {
     float r[CH];
     int32_t idx[CH];
     uint32_t mask[CH][W];
-    __align__(1024) uint8_t u[GramScratch<F, ENG>::value];
-    uint64_t bar;
+    __align__(1024) uint8_t u[ENG == ENG_CUDA ? kCtaWarps * F * (F + 1) * 4 : 16];
+    __align__(1024) uint8_t tiles[TileBytes<F, ENG>::value];
+    uint64_t bars[2];
     uint32_t tmem_slot;
 };
 
-// Masked Gram of one chunk into part[c] (or masks only when mode == 2).
+// Masked Gram of split chunks into part[c] (or masks only when mode == 2);
+// persistent over chunks with a tensor-core engine (as k_cta_rows).
 template <int F, int ENG>
 __global__ void __launch_bounds__(kCtaThreads) k_split_gram(Side side, Params p, SplitPlan sp, SplitState st,
                                                             int mode, uint32_t* __restrict__ masks_out) {
@@ -572,19 +602,53 @@ __global__ void __launch_bounds__(kCtaThreads) k_split_gram(Side side, Params p,
     using Smem = SplitGramSmem<F, ENG>;
     Smem& S = *reinterpret_cast<Smem*>(smem_raw);
     constexpr int W = Smem::W;
+    constexpr bool TC = ENG != ENG_CUDA;
+    constexpr int PREC = TC ? tc_prec(ENG) : 0;
     const int tid = threadIdx.x;
-    const int c = blockIdx.x;
-    const ChunkInfo ci = chunk_info<F>(sp, side, c);
-    stage_tile<F>(S.x, S.r, S.idx, side, p.f, ci.lo + ci.start, ci.len);
-    const int sa = ci.slot * F + tid % F;
-    build_masks<F>(S.mask, S.x, ci.len, ci.start, st.P[sa], st.Mk[sa], st.cut[sa]);
-    __syncthreads();
-    if (masks_out != nullptr)
-        for (int e = tid; e < ci.len * W; e += kCtaThreads) masks_out[(ci.lo + ci.start) * W + e] = (&S.mask[0][0])[e];
-    if (mode == 2) return;
-    float* dst = st.part + (int64_t)c * F * (F + 1);
-    gram_tile<F, ENG>(S.u, &S.bar, &S.tmem_slot, S.x, S.mask, S.r, ci.len, p.gram_mode == GRAM_SYM,
-                      [&](int a, int cc, float v) { dst[a * (F + 1) + cc] = v; });
+    const bool sym = p.gram_mode == GRAM_SYM;
+    TcPipe P;
+    if constexpr (TC) {
+        if (mode != 2 && blockIdx.x < sp.n_chunks) tc_pipe_setup<F, PREC>(S.tiles, S.bars, &S.tmem_slot, P);
+    }
+    int prev_c = -1, prev_acc = 0, prev_len = 0, iter = 0;
+    auto finish_prev = [&]() {
+        if constexpr (TC) {
+            if (prev_c < 0) return;
+            float* dst = st.part + (int64_t)prev_c * F * (F + 1);
+            tc_pipe_finish<F, PREC>(P, S.bars, prev_acc, prev_len == 0,
+                                    [&](int a, int cc, float v) { dst[a * (F + 1) + cc] = v; });
+            prev_c = -1;
+        }
+    };
+    for (int c = blockIdx.x; c < sp.n_chunks; c += gridDim.x, ++iter) {
+        __syncthreads();
+        const ChunkInfo ci = chunk_info<F>(sp, side, c);
+        stage_tile<F>(S.x, S.r, S.idx, side, p.f, ci.lo + ci.start, ci.len);
+        const int sa = ci.slot * F + tid % F;
+        build_masks<F>(S.mask, S.x, ci.len, ci.start, st.P[sa], st.Mk[sa], st.cut[sa]);
+        __syncthreads();
+        if (masks_out != nullptr)
+            for (int e = tid; e < ci.len * W; e += kCtaThreads)
+                masks_out[(ci.lo + ci.start) * W + e] = (&S.mask[0][0])[e];
+        if (mode == 2) continue;
+        if constexpr (TC) {
+            finish_prev();
+            tc_pipe_row<F, PREC, W>(P, S.tiles, S.bars, S.x, S.mask, S.r, ci.len, sym, iter & 1);
+            prev_c = c;
+            prev_acc = iter & 1;
+            prev_len = ci.len;
+        } else {
+            float* dst = st.part + (int64_t)c * F * (F + 1);
+            gram_tile<F, ENG>(S.u, nullptr, nullptr, S.x, S.mask, S.r, ci.len, sym,
+                              [&](int a, int cc, float v) { dst[a * (F + 1) + cc] = v; });
+        }
+    }
+    if constexpr (TC) {
+        if (mode != 2 && blockIdx.x < sp.n_chunks) {
+            finish_prev();
+            tc_pipe_teardown<F, PREC>(P);
+        }
+    }
 }
 
 // Sum the chunk Grams of each slot in chunk order, add the regulariser.

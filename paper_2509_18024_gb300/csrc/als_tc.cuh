@@ -46,7 +46,8 @@ struct TcCfg {
     static constexpr int ESZ = PREC == TC_BF16 ? 2 : 4;
     static constexpr int KC = 16 / ESZ;              // elements per 16-byte core-matrix row
     static constexpr int KSTEP = 32 / ESZ;           // K of one instruction (32 bytes)
-    static constexpr int KT = PREC == TC_TF32X3 ? 32 : 64;  // positions per staged chunk
+    // positions per staged chunk (two tile buffers must fit with the slice)
+    static constexpr int KT = PREC == TC_BF16 ? 64 : (PREC == TC_TF32 ? 32 : 16);
     static constexpr int NSPLIT = PREC == TC_TF32X3 ? 2 : 1;  // hi (and lo) copies
     static constexpr int A_BYTES = M * KT * ESZ;
     static constexpr int B_BYTES = N * KT * ESZ;
@@ -81,39 +82,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
     return done != 0;
 }
 
-// Allocate TMEM and init the barrier (all threads of the CTA; ends in a barrier).
-template <int F, int PREC>
-__device__ __forceinline__ void tc_setup(uint8_t* tiles, uint64_t* bar, uint32_t* tmem_slot, TcCtx& ctx) {
-    using C = TcCfg<F, PREC>;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    // Padding rows of A (>= F) and of B (> F) are zero for the whole kernel.
-    uint32_t* t32 = reinterpret_cast<uint32_t*>(tiles);
-    for (int e = tid; e < C::TILE_BYTES / 4; e += blockDim.x) t32[e] = 0u;
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)));
-        asm volatile("fence.mbarrier_init.release.cluster;");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
-                     "r"(C::TMEM_COLS));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    ctx.tmem = *tmem_slot;
-    ctx.phase = 0;
-    ctx.ok = true;
-}
-
-template <int F, int PREC>
-__device__ __forceinline__ void tc_teardown(const TcCtx& ctx) {
-    using C = TcCfg<F, PREC>;
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    if ((threadIdx.x >> 5) == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(ctx.tmem), "r"(C::TMEM_COLS));
-}
-
 // Write one 16-byte operand row (KC consecutive positions of one feature).
 template <int PREC>
 __device__ __forceinline__ void put16(uint8_t* dst, const float (&v)[8], int kc) {
@@ -131,111 +99,6 @@ __device__ __forceinline__ void put16(uint8_t* dst, const float (&v)[8], int kc)
         *reinterpret_cast<uint4*>(dst) = u;
     }
     (void)kc;
-}
-
-// Accumulate positions [k_begin, k_end) of a staged tile into the TMEM
-// accumulator (first == true starts it from zero). x: [*][F] row-major,
-// mask: W words per position, r: ratings. All threads call it.
-template <int F, int PREC, int W>
-__device__ __forceinline__ void tc_accumulate(TcCtx& ctx, uint8_t* tiles, uint64_t* bar, const float (*x)[F],
-                                              const uint32_t (*mask)[W], const float* r, int k_begin, int k_end,
-                                              bool sym, bool first) {
-    using C = TcCfg<F, PREC>;
-    const int tid = threadIdx.x;
-    uint8_t* A0 = tiles;
-    uint8_t* B0 = tiles + C::A_BYTES;
-    uint8_t* A1 = tiles + C::A_BYTES + C::B_BYTES;  // lo copies (split-TF32 only)
-    uint8_t* B1 = A1 + C::A_BYTES;
-    constexpr int KC = C::KC;
-    constexpr int GROUPS = C::KT / KC;  // 16-byte rows per feature per chunk
-    bool started = !first;
-    for (int c0 = k_begin; c0 < k_end; c0 += C::KT) {
-        // Operand rows: (feature or rhs row m, 16-byte group g). Rows 0..F-1
-        // of A are masked features, rows 0..F-1 of B plain features (masked
-        // for the symmetric variant), row F of B the ratings.
-        for (int e = tid; e < (F + 1) * GROUPS; e += blockDim.x) {
-            const int m = e % (F + 1), g = e / (F + 1);
-            float va[8], vb[8], la[8], lb[8];
-#pragma unroll
-            for (int q = 0; q < KC; ++q) {
-                const int k = c0 + g * KC + q;
-                float xv = 0.f, keep = 0.f;
-                if (k < k_end) {
-                    if (m < F) {
-                        xv = x[k][m];
-                        keep = ((mask[k][m >> 5] >> (m & 31)) & 1u) ? 1.f : 0.f;
-                    } else {
-                        xv = r[k];
-                        keep = 1.f;
-                    }
-                }
-                const float a = keep * xv;
-                const float b = (m < F && sym) ? a : xv;
-                if (PREC == TC_TF32X3) {
-                    const float ah = __uint_as_float(tf32_rna(a)), bh = __uint_as_float(tf32_rna(b));
-                    va[q] = ah;
-                    vb[q] = bh;
-                    la[q] = __uint_as_float(tf32_rna(a - ah));
-                    lb[q] = __uint_as_float(tf32_rna(b - bh));
-                } else if (PREC == TC_TF32) {
-                    va[q] = __uint_as_float(tf32_rna(a));
-                    vb[q] = __uint_as_float(tf32_rna(b));
-                } else {
-                    va[q] = a;
-                    vb[q] = b;
-                }
-            }
-            if (m < F) put16<PREC>(A0 + C::off(C::M, m, g * KC), va, KC);
-            put16<PREC>(B0 + C::off(C::N, m, g * KC), vb, KC);
-            if (PREC == TC_TF32X3) {
-                if (m < F) put16<PREC>(A1 + C::off(C::M, m, g * KC), la, KC);
-                put16<PREC>(B1 + C::off(C::N, m, g * KC), lb, KC);
-            }
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;");
-#pragma unroll
-            for (int ks = 0; ks < C::KT / C::KSTEP; ++ks) {
-                // Two 16-byte K groups per instruction.
-                const uint32_t koff_a = (uint32_t)(2 * ks) * (C::M / 8) * 128;
-                const uint32_t koff_b = (uint32_t)(2 * ks) * (C::N / 8) * 128;
-                const int nterm = PREC == TC_TF32X3 ? 3 : 1;
-#pragma unroll
-                for (int t = 0; t < nterm; ++t) {
-                    // split-TF32 terms: hi*hi, hi*lo, lo*hi
-                    const uint8_t* Ap = (t == 2) ? A1 : A0;
-                    const uint8_t* Bp = (t == 1) ? B1 : B0;
-                    const uint64_t ad = umma_desc(smem_addr(Ap) + koff_a, (C::M / 8) * 128, 128);
-                    const uint64_t bd = umma_desc(smem_addr(Bp) + koff_b, (C::N / 8) * 128, 128);
-                    const uint32_t acc = started ? 1u : 0u;
-                    if (PREC == TC_BF16)
-                        asm volatile(
-                            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(ctx.tmem),
-                            "l"(ad), "l"(bd), "r"(C::IDESC), "r"(acc));
-                    else
-                        asm volatile(
-                            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(ctx.tmem),
-                            "l"(ad), "l"(bd), "r"(C::IDESC), "r"(acc));
-                    started = true;
-                }
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_addr(bar)));
-        }
-        started = true;
-        // The tile is rewritten by the next chunk: wait until the MMAs read it.
-        if (!mbar_wait(bar, ctx.phase)) ctx.ok = false;
-        ctx.phase ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-    }
-    if (!started && tid == 0) {
-        // Nothing was accumulated (empty range): the caller reads zeros via
-        // tc_store's `empty` flag.
-    }
 }
 
 // Read the accumulator rows 0..F-1, columns 0..F (G and rhs) and hand each
@@ -261,6 +124,169 @@ __device__ __forceinline__ void tc_store(const TcCtx& ctx, bool empty, Store sto
                 if (c0 + j <= F) store(a, c0 + j, (empty || !ctx.ok) ? 0.f : __uint_as_float(v[j]));
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Pipelined, persistent form: two operand tile buffers (each with its own
+// completion barrier) and two TMEM accumulators. Converting chunk c + 1 runs
+// while the MMAs of chunk c execute; a buffer is rewritten only after the
+// commit that last read it completed, so no barrier ever runs two phases
+// ahead of its waiter.
+struct TcPipe {
+    uint32_t tmem;    // base of the two accumulators
+    uint32_t ph[2];   // parity of the next completion per buffer
+    int pend[2];      // a commit on this buffer is outstanding
+    int next;         // buffer the next chunk uses
+    bool ok;          // false once a bounded wait ran out
+};
+
+template <int F, int PREC>
+__device__ __forceinline__ void tc_pipe_setup(uint8_t* tiles, uint64_t* bars, uint32_t* tmem_slot, TcPipe& P) {
+    using C = TcCfg<F, PREC>;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    uint32_t* t32 = reinterpret_cast<uint32_t*>(tiles);
+    for (int e = tid; e < 2 * C::TILE_BYTES / 4; e += blockDim.x) t32[e] = 0u;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bars[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bars[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
+                     "r"(2 * C::TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    P.tmem = *tmem_slot;
+    P.ph[0] = P.ph[1] = 0u;
+    P.pend[0] = P.pend[1] = 0;
+    P.next = 0;
+    P.ok = true;
+}
+
+__device__ __forceinline__ void tc_pipe_drain(TcPipe& P, uint64_t* bars, int b) {
+    if (P.pend[b]) {
+        if (!mbar_wait(&bars[b], P.ph[b])) P.ok = false;
+        P.ph[b] ^= 1u;
+        P.pend[b] = 0;
+    }
+}
+
+// Accumulate positions [0, n) of a staged tile into accumulator `acc`
+// (0 or 1), starting it from zero. All threads call it; MMAs stay in flight.
+template <int F, int PREC, int W>
+__device__ __forceinline__ void tc_pipe_row(TcPipe& P, uint8_t* tiles, uint64_t* bars, const float (*x)[F],
+                                            const uint32_t (*mask)[W], const float* r, int n, bool sym, int acc) {
+    using C = TcCfg<F, PREC>;
+    const int tid = threadIdx.x;
+    constexpr int KC = C::KC;
+    constexpr int GROUPS = C::KT / KC;
+    const uint32_t dacc = P.tmem + (uint32_t)acc * C::TMEM_COLS;
+    for (int c0 = 0; c0 < n; c0 += C::KT) {
+        const int b = P.next;
+        P.next ^= 1;
+        tc_pipe_drain(P, bars, b);
+        uint8_t* A0 = tiles + b * C::TILE_BYTES;
+        uint8_t* B0 = A0 + C::A_BYTES;
+        uint8_t* A1 = B0 + C::B_BYTES;
+        uint8_t* B1 = A1 + C::A_BYTES;
+        for (int e = tid; e < (F + 1) * GROUPS; e += blockDim.x) {
+            const int m = e % (F + 1), g = e / (F + 1);
+            float va[8], vb[8], la[8], lb[8];
+#pragma unroll
+            for (int q = 0; q < KC; ++q) {
+                const int k = c0 + g * KC + q;
+                float xv = 0.f, keep = 0.f;
+                if (k < n) {
+                    if (m < F) {
+                        xv = x[k][m];
+                        keep = ((mask[k][m >> 5] >> (m & 31)) & 1u) ? 1.f : 0.f;
+                    } else {
+                        xv = r[k];
+                        keep = 1.f;
+                    }
+                }
+                const float a = keep * xv;
+                const float bv = (m < F && sym) ? a : xv;
+                if (PREC == TC_TF32X3) {
+                    const float ah = __uint_as_float(tf32_rna(a)), bh = __uint_as_float(tf32_rna(bv));
+                    va[q] = ah;
+                    vb[q] = bh;
+                    la[q] = __uint_as_float(tf32_rna(a - ah));
+                    lb[q] = __uint_as_float(tf32_rna(bv - bh));
+                } else if (PREC == TC_TF32) {
+                    va[q] = __uint_as_float(tf32_rna(a));
+                    vb[q] = __uint_as_float(tf32_rna(bv));
+                } else {
+                    va[q] = a;
+                    vb[q] = bv;
+                }
+            }
+            if (m < F) put16<PREC>(A0 + C::off(C::M, m, g * KC), va, KC);
+            put16<PREC>(B0 + C::off(C::N, m, g * KC), vb, KC);
+            if (PREC == TC_TF32X3) {
+                if (m < F) put16<PREC>(A1 + C::off(C::M, m, g * KC), la, KC);
+                put16<PREC>(B1 + C::off(C::N, m, g * KC), lb, KC);
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+            for (int ks = 0; ks < C::KT / C::KSTEP; ++ks) {
+                const uint32_t koff_a = (uint32_t)(2 * ks) * (C::M / 8) * 128;
+                const uint32_t koff_b = (uint32_t)(2 * ks) * (C::N / 8) * 128;
+                const int nterm = PREC == TC_TF32X3 ? 3 : 1;
+#pragma unroll
+                for (int t = 0; t < nterm; ++t) {
+                    const uint8_t* Ap = (t == 2) ? A1 : A0;
+                    const uint8_t* Bp = (t == 1) ? B1 : B0;
+                    const uint64_t ad = umma_desc(smem_addr(Ap) + koff_a, (C::M / 8) * 128, 128);
+                    const uint64_t bd = umma_desc(smem_addr(Bp) + koff_b, (C::N / 8) * 128, 128);
+                    const uint32_t accum = (c0 > 0 || ks > 0 || t > 0) ? 1u : 0u;
+                    if (PREC == TC_BF16)
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dacc),
+                            "l"(ad), "l"(bd), "r"(C::IDESC), "r"(accum));
+                    else
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(dacc),
+                            "l"(ad), "l"(bd), "r"(C::IDESC), "r"(accum));
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_addr(&bars[b])));
+        }
+        P.pend[b] = 1;
+    }
+}
+
+// Wait for every outstanding MMA, then read accumulator `acc` (rows 0..F-1,
+// columns 0..F) into store(a, c, v); `empty` rows store zeros.
+template <int F, int PREC, class Store>
+__device__ __forceinline__ void tc_pipe_finish(TcPipe& P, uint64_t* bars, int acc, bool empty, Store store) {
+    using C = TcCfg<F, PREC>;
+    tc_pipe_drain(P, bars, 0);
+    tc_pipe_drain(P, bars, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    TcCtx ctx;
+    ctx.tmem = P.tmem + (uint32_t)acc * C::TMEM_COLS;
+    ctx.phase = 0;
+    ctx.ok = P.ok;
+    tc_store<F, PREC>(ctx, empty, store);
+}
+
+template <int F, int PREC>
+__device__ __forceinline__ void tc_pipe_teardown(const TcPipe& P) {
+    using C = TcCfg<F, PREC>;
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(P.tmem), "r"(2 * C::TMEM_COLS));
 }
 
 }  // namespace als

@@ -161,17 +161,12 @@ __device__ __forceinline__ void warp_solve(float (&v)[F], float rhs, int f, bool
     for (int k = 0; k < F; ++k) {
         int bl;
         if (pivot) {
-            float best = active ? fabsf(v[k]) : -1.f;
-            bl = lane;
-#pragma unroll
-            for (int o = 16; o; o >>= 1) {
-                float ob = __shfl_xor_sync(kFull, best, o);
-                int ol = __shfl_xor_sync(kFull, bl, o);
-                if (ob > best || (ob == best && ol < bl)) {
-                    best = ob;
-                    bl = ol;
-                }
-            }
+            // Largest |a_ik| over the remaining rows, lowest lane on ties:
+            // the bit patterns of non-negative floats sort like their values
+            // (+1 keeps inactive lanes, 0, below every candidate).
+            const uint32_t key = active ? (__float_as_uint(fabsf(v[k])) + 1u) : 0u;
+            const uint32_t best = __reduce_max_sync(kFull, key);
+            bl = __ffs(__ballot_sync(kFull, key == best)) - 1;
         } else {
             bl = k;
         }
@@ -342,6 +337,49 @@ __device__ __forceinline__ BinPick warp_pick_bin64(uint32_t* bins, uint32_t need
         r.digit = 2 * lane;
         r.newneed = need - above - c1;
         r.inbin = c0;
+    }
+    r.digit = __shfl_sync(kFull, r.digit, L);
+    r.newneed = __shfl_sync(kFull, r.newneed, L);
+    r.inbin = __shfl_sync(kFull, r.inbin, L);
+    return r;
+}
+
+// Half-warp form: lanes 0..15 and 16..31 each scan the 64 bins of their own
+// column (lane h of a half holds bins 4h..4h+3) and clear them; `act` false
+// marks an idle half (no column: nothing read or cleared, result unused).
+__device__ __forceinline__ BinPick half_pick_bin64(uint32_t* bins, uint32_t need, bool act) {
+    const int lane = threadIdx.x & 31, h = lane & 15;
+    uint32_t c[4] = {0u, 0u, 0u, 0u};
+    if (act) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            c[q] = bins[hist64_slot(4 * h + q)];
+            bins[hist64_slot(4 * h + q)] = 0u;
+        }
+    }
+    const uint32_t lsum = c[0] + c[1] + c[2] + c[3];
+    uint32_t incl = lsum;
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) {
+        const uint32_t t = __shfl_down_sync(kFull, incl, o, 16);
+        if (h + o < 16) incl += t;
+    }
+    const uint32_t above = incl - lsum;
+    const unsigned ob = __ballot_sync(kFull, act && above < need && need <= incl);
+    const unsigned mine = (lane < 16) ? (ob & 0xffffu) : (ob >> 16);
+    const int L = (mine ? __ffs(mine) - 1 : 0) + (lane & 16);
+    BinPick r{0, 0u, 0u};
+    uint32_t cum = above;
+    bool found = false;
+#pragma unroll
+    for (int q = 3; q >= 0; --q) {
+        if (!found && cum + c[q] >= need) {
+            r.digit = 4 * h + q;
+            r.newneed = need - cum;
+            r.inbin = c[q];
+            found = true;
+        }
+        if (!found) cum += c[q];
     }
     r.digit = __shfl_sync(kFull, r.digit, L);
     r.newneed = __shfl_sync(kFull, r.newneed, L);

@@ -157,7 +157,7 @@ namespace als {
 // identity). Warp per system; rows[w] gives the output row, or w itself when
 // rows is null.
 template <int F>
-__global__ void __launch_bounds__(256) k_solve_rows(const float* __restrict__ G_aug, const int32_t* __restrict__ rows,
+__global__ void __launch_bounds__(256, 4) k_solve_rows(const float* __restrict__ G_aug, const int32_t* __restrict__ rows,
                                                     int n_list, Params p, float* __restrict__ X_out,
                                                     int32_t* __restrict__ flags_out, Counters* cnt, Fallback fb) {
     __shared__ float tile[8][F][F + 1];
@@ -165,7 +165,8 @@ __global__ void __launch_bounds__(256) k_solve_rows(const float* __restrict__ G_
     const int w = blockIdx.x * 8 + warp;
     if (w >= n_list) return;
     const float* src = G_aug + (int64_t)w * F * (F + 1);
-    for (int e = lane; e < F * (F + 1); e += 32) tile[warp][e / (F + 1)][e % (F + 1)] = src[e];
+    float* t = &tile[warp][0][0];  // the tile is contiguous with the same layout
+    for (int e = lane; e < F * (F + 1); e += 32) t[e] = __ldg(src + e);
     __syncwarp();
     float v[F];
 #pragma unroll

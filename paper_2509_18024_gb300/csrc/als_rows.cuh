@@ -58,10 +58,38 @@ struct GramAcc {
         for (int k = k_begin; k < k_end; k += k_step) {
             const uint32_t m = mask[k];
             float xa[TA], xb[TB];
+            if constexpr (TA % 4 == 0 && TB % 4 == 0) {
+                // 16-byte loads: a0 and b0 are multiples of 4.
+                const float4* row = reinterpret_cast<const float4*>(x[k]);
 #pragma unroll
-            for (int q = 0; q < TA; ++q) xa[q] = ((m >> (a0 + q)) & 1u) ? x[k][a0 + q] : 0.f;
+                for (int q = 0; q < TA / 4; ++q) {
+                    const float4 v = row[a0 / 4 + q];
+                    xa[4 * q] = v.x;
+                    xa[4 * q + 1] = v.y;
+                    xa[4 * q + 2] = v.z;
+                    xa[4 * q + 3] = v.w;
+                }
 #pragma unroll
-            for (int t = 0; t < TB; ++t) xb[t] = (!sym || ((m >> (b0 + t)) & 1u)) ? x[k][b0 + t] : 0.f;
+                for (int t = 0; t < TB / 4; ++t) {
+                    const float4 v = row[b0 / 4 + t];
+                    xb[4 * t] = v.x;
+                    xb[4 * t + 1] = v.y;
+                    xb[4 * t + 2] = v.z;
+                    xb[4 * t + 3] = v.w;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < TA; ++q) xa[q] = x[k][a0 + q];
+#pragma unroll
+                for (int t = 0; t < TB; ++t) xb[t] = x[k][b0 + t];
+            }
+            const uint32_t ma = m >> a0, mb = m >> b0;
+#pragma unroll
+            for (int q = 0; q < TA; ++q) xa[q] = ((ma >> q) & 1u) ? xa[q] : 0.f;
+            if (sym) {
+#pragma unroll
+                for (int t = 0; t < TB; ++t) xb[t] = ((mb >> t) & 1u) ? xb[t] : 0.f;
+            }
             const float rk = r[k];
 #pragma unroll
             for (int q = 0; q < TA; ++q) {
@@ -251,6 +279,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_cta_rows(Side side, Params p, c
     const int a_t = tid % F;  // thread t always handles column t mod F
     const int k0 = tid / F;
     constexpr int kstep = kCtaThreads / F;
+    static_assert(F % kCtaWarps == 0, "the bin scans give each warp F / kCtaWarps columns");
     uint32_t (*hist)[kHist64Row] = S.hist();
 
     if (tid < F) {
@@ -287,10 +316,15 @@ __global__ void __launch_bounds__(kCtaThreads) k_cta_rows(Side side, Params p, c
             }
         }
         __syncthreads();
-        for (int a = warp; a < F; a += kCtaWarps) {
-            if (S.done[a] || S.eres[a]) continue;
-            const BinPick bp = warp_pick_bin64(hist[a], (uint32_t)S.need[a]);
-            if (lane == 0) {
+        // Two columns per warp scan (a half-warp each).
+        for (int j = 0; j < F / kCtaWarps; j += 2) {
+            const int ca = warp + kCtaWarps * j;
+            const int cb = (j + 1 < F / kCtaWarps) ? ca + kCtaWarps : -1;
+            const int a = (lane < 16) ? ca : cb;
+            const bool act = a >= 0 && !S.done[a] && !S.eres[a];
+            if (!__any_sync(kFull, act)) continue;
+            const BinPick bp = half_pick_bin64(hist[act ? a : ca], act ? (uint32_t)S.need[a] : 0u, act);
+            if ((lane & 15) == 0 && act) {
                 const int T = (int)S.wtop[a];
                 if (bp.digit >= 1) {
                     S.P[a] = (uint32_t)(T - 64 + bp.digit) << 23;
@@ -324,10 +358,14 @@ __global__ void __launch_bounds__(kCtaThreads) k_cta_rows(Side side, Params p, c
             }
         }
         __syncthreads();
-        for (int a = warp; a < F; a += kCtaWarps) {
-            if (S.done[a]) continue;
-            const BinPick bp = warp_pick_bin64(hist[a], (uint32_t)S.need[a]);
-            if (lane == 0) {
+        for (int j = 0; j < F / kCtaWarps; j += 2) {
+            const int ca = warp + kCtaWarps * j;
+            const int cb = (j + 1 < F / kCtaWarps) ? ca + kCtaWarps : -1;
+            const int a = (lane < 16) ? ca : cb;
+            const bool act = a >= 0 && !S.done[a];
+            if (!__any_sync(kFull, act)) continue;
+            const BinPick bp = half_pick_bin64(hist[act ? a : ca], act ? (uint32_t)S.need[a] : 0u, act);
+            if ((lane & 15) == 0 && act) {
                 S.P[a] |= (uint32_t)bp.digit << sh;
                 S.Mk[a] = man_after(m);
                 S.need[a] = (int)bp.newneed;

@@ -111,7 +111,10 @@ struct GramAcc {
     }
 };
 
-// Stage positions [0, cn) of the slice starting at absolute entry e0.
+// Stage positions [0, cn) of the slice starting at absolute entry e0. With
+// f == F and a 16-byte aligned Y, each thread moves whole float4 quarters of
+// rows (eight threads per 128-byte row at F = 32); else one float each, zero
+// in the padding columns a >= f.
 template <int F>
 __device__ __forceinline__ void stage_tile(float (*x)[F], float* r, int32_t* idx, const Side& side, int f,
                                            int64_t e0, int cn) {
@@ -120,19 +123,39 @@ __device__ __forceinline__ void stage_tile(float (*x)[F], float* r, int32_t* idx
         r[k] = side.values[e0 + k];
     }
     __syncthreads();
-    const int total = cn * F;
-    for (int e0 = threadIdx.x; e0 < total; e0 += kCtaThreads * kGatherBatch) {
-        float v[kGatherBatch];
+    if (f == F && (reinterpret_cast<uintptr_t>(side.Y) & 15u) == 0) {
+        constexpr int Q = F / 4;  // float4 per row
+        constexpr int B = 4;      // independent gathers in flight per thread
+        const int total = cn * Q;
+        for (int g0 = threadIdx.x; g0 < total; g0 += kCtaThreads * B) {
+            float4 v[B];
 #pragma unroll
-        for (int u = 0; u < kGatherBatch; ++u) {
-            const int e = e0 + u * kCtaThreads;
-            const int k = e / F, a = e % F;
-            v[u] = (e < total && a < f) ? __ldg(side.Y + (int64_t)idx[k] * f + a) : 0.f;
+            for (int u = 0; u < B; ++u) {
+                const int g = g0 + u * kCtaThreads;
+                v[u] = g < total ? __ldg(reinterpret_cast<const float4*>(side.Y + (int64_t)idx[g / Q] * F) + g % Q)
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < B; ++u) {
+                const int g = g0 + u * kCtaThreads;
+                if (g < total) reinterpret_cast<float4*>(x[g / Q])[g % Q] = v[u];
+            }
         }
+    } else {
+        const int total = cn * F;
+        for (int g0 = threadIdx.x; g0 < total; g0 += kCtaThreads * kGatherBatch) {
+            float v[kGatherBatch];
 #pragma unroll
-        for (int u = 0; u < kGatherBatch; ++u) {
-            const int e = e0 + u * kCtaThreads;
-            if (e < total) x[e / F][e % F] = v[u];
+            for (int u = 0; u < kGatherBatch; ++u) {
+                const int e = g0 + u * kCtaThreads;
+                const int k = e / F, a = e % F;
+                v[u] = (e < total && a < f) ? __ldg(side.Y + (int64_t)idx[k] * f + a) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < kGatherBatch; ++u) {
+                const int e = g0 + u * kCtaThreads;
+                if (e < total) x[e / F][e % F] = v[u];
+            }
         }
     }
     __syncthreads();
@@ -158,24 +181,43 @@ __device__ __forceinline__ void init_column(int a, int f, long long s, long long
 }
 
 // ---------------------------------------------------------------------------
-// Keep masks of a staged tile: thread (k, a_t) applies its column's keep
-// rule, a ballot packs the bits. pos0 = position of tile row 0 in its row.
+// Keep masks of a staged tile: thread (k, g) applies the keep rules of
+// columns 4g..4g+3 (state P, Mk, cut indexed by column) to one float4 of
+// position k; the nibbles of one mask word meet by an OR over the (up to 8)
+// neighbouring lanes of that position. pos0 = position of tile row 0 in its
+// row.
 template <int F>
 __device__ __forceinline__ void build_masks(uint32_t (*mask)[MaskWords<F>::value], const float (*x)[F], int cn,
-                                            int pos0, uint32_t Pa, uint32_t Ma, int cuta) {
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int a_t = tid % F, k0 = tid / F;
-    constexpr int kstep = kCtaThreads / F;
+                                            int pos0, const uint32_t* P, const uint32_t* Mk, const int32_t* cut) {
+    static_assert(F % 4 == 0 && F / 4 <= 32, "a position's quarters sit in one warp");
+    constexpr int T4 = F / 4;                  // threads per position
+    constexpr int GW = T4 < 8 ? T4 : 8;        // threads per mask word
+    constexpr int kstep = kCtaThreads / T4;    // positions per pass of the CTA
+    const int tid = threadIdx.x;
+    const int g = tid % T4, k0 = tid / T4;
+    uint32_t Pc[4], Mc[4];
+    int Cc[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        Pc[c] = P[4 * g + c];
+        Mc[c] = Mk[4 * g + c];
+        Cc[c] = cut[4 * g + c];
+    }
     for (int kk = 0; kk < cn; kk += kstep) {
         const int k = kk + k0;
-        const bool keep = k < cn && keep_rule(mag_key(x[k][a_t]), Pa, Ma, pos0 + k, cuta);
-        const unsigned b = __ballot_sync(kFull, keep);
-        if constexpr (F >= 32) {
-            if (lane == 0 && k < cn) mask[k][a_t >> 5] = b;
-        } else {
-            const uint32_t fmask = (1u << F) - 1u;
-            if (a_t == 0 && k < cn) mask[k][0] = (b >> (lane & ~(F - 1))) & fmask;
+        uint32_t nib = 0u;
+        if (k < cn) {
+            const float4 v = reinterpret_cast<const float4*>(x[k])[g];
+            const int pos = pos0 + k;
+            nib = (uint32_t)keep_rule(mag_key(v.x), Pc[0], Mc[0], pos, Cc[0]) |
+                  ((uint32_t)keep_rule(mag_key(v.y), Pc[1], Mc[1], pos, Cc[1]) << 1) |
+                  ((uint32_t)keep_rule(mag_key(v.z), Pc[2], Mc[2], pos, Cc[2]) << 2) |
+                  ((uint32_t)keep_rule(mag_key(v.w), Pc[3], Mc[3], pos, Cc[3]) << 3);
         }
+        uint32_t word = nib << (4 * (g % GW));
+#pragma unroll
+        for (int o = 1; o < GW; o <<= 1) word |= __shfl_xor_sync(kFull, word, o);
+        if (k < cn && g % GW == 0) mask[k][g / 8] = word;
     }
 }
 
@@ -299,9 +341,11 @@ __global__ void __launch_bounds__(kCtaThreads) k_cta_rows(Side side, Params p, c
     stage_tile<F>(S.x, S.r, S.idx, side, f, lo, n);
     {
         // Window top of each column: its largest exponent + 1.
-        uint32_t em = 0u;
-        for (int k = k0; k < n; k += kstep) em = max(em, mag_key(S.x[k][a_t]) >> 23);
-        atomicMax(&S.wtop[a_t], em + 1u);
+        if (!S.done[a_t]) {
+            uint32_t em = 0u;
+            for (int k = k0; k < n; k += kstep) em = max(em, mag_key(S.x[k][a_t]) >> 23);
+            atomicMax(&S.wtop[a_t], em + 1u);
+        }
     }
     __syncthreads();
 
@@ -398,7 +442,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_cta_rows(Side side, Params p, c
         if (lane == 0) S.cut[a] = cut;
     }
     __syncthreads();
-    build_masks<F>(S.mask, S.x, n, 0, S.P[a_t], S.Mk[a_t], S.cut[a_t]);
+    build_masks<F>(S.mask, S.x, n, 0, S.P, S.Mk, S.cut);
     __syncthreads();
     if (masks_out != nullptr)
         for (int e = tid; e < n * W; e += kCtaThreads) masks_out[lo * W + e] = (&S.mask[0][0])[e];
@@ -503,26 +547,57 @@ __global__ void __launch_bounds__(kCtaThreads) k_split_hist(Side side, Params p,
     const int len = min(kSplitSuper, n - start);
     for (int e = tid; e < F * kHistRow; e += kCtaThreads) (&hist[0][0])[e] = 0u;
     __syncthreads();
-    const int a_t = tid % F, k0 = tid / F;
-    constexpr int kstep = kCtaThreads / F;
-    const int sa = slot * F + a_t;
-    if (!st.done[sa]) {
-        const uint32_t Pa = st.P[sa], hm = radix_before(pass);
-        const int64_t e0 = lo + start;
-        for (int kb = k0; kb < len; kb += kstep * kGatherBatch) {
-            int32_t j[kGatherBatch];
-            uint32_t key[kGatherBatch];
+    // Thread (k, q) covers columns 4q..4q+3 of positions k0, k0 + kstep, ...:
+    // one index load and one float4 gather (f == F, aligned Y) per position.
+    constexpr int T4 = F / 4;
+    constexpr int kstep = kCtaThreads / T4;
+    const int q = tid % T4, k0 = tid / T4;
+    const int sa = slot * F + 4 * q;
+    bool open[4];
+    uint32_t Pc[4];
+    bool any = false;
 #pragma unroll
-            for (int u = 0; u < kGatherBatch; ++u) {
+    for (int c = 0; c < 4; ++c) {
+        open[c] = !st.done[sa + c];
+        Pc[c] = st.P[sa + c];
+        any |= open[c];
+    }
+    if (any) {
+        const uint32_t hm = radix_before(pass);
+        const int64_t e0 = lo + start;
+        const int f = p.f;
+        const bool vec = f == F && (reinterpret_cast<uintptr_t>(side.Y) & 15u) == 0;
+        constexpr int B = 4;
+        for (int kb = k0; kb < len; kb += kstep * B) {
+            int32_t j[B];
+#pragma unroll
+            for (int u = 0; u < B; ++u) {
                 const int k = kb + u * kstep;
                 j[u] = k < len ? side.indices[e0 + k] : -1;
             }
+            float4 v[B];
 #pragma unroll
-            for (int u = 0; u < kGatherBatch; ++u)
-                key[u] = j[u] >= 0 ? mag_key(__ldg(side.Y + (int64_t)j[u] * p.f + a_t)) : 0u;
+            for (int u = 0; u < B; ++u) {
+                if (j[u] < 0) {
+                    v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                } else if (vec) {
+                    v[u] = __ldg(reinterpret_cast<const float4*>(side.Y + (int64_t)j[u] * F) + q);
+                } else {
+                    const float* y = side.Y + (int64_t)j[u] * f;
+                    const int a = 4 * q;
+                    v[u] = make_float4(a < f ? __ldg(y + a) : 0.f, a + 1 < f ? __ldg(y + a + 1) : 0.f,
+                                       a + 2 < f ? __ldg(y + a + 2) : 0.f, a + 3 < f ? __ldg(y + a + 3) : 0.f);
+                }
+            }
 #pragma unroll
-            for (int u = 0; u < kGatherBatch; ++u)
-                if (j[u] >= 0 && (key[u] & hm) == Pa) atomicAdd(&hist[a_t][hist_slot(radix_digit(key[u], pass))], 1u);
+            for (int u = 0; u < B; ++u) {
+                if (j[u] < 0) continue;
+                const uint32_t key[4] = {mag_key(v[u].x), mag_key(v[u].y), mag_key(v[u].z), mag_key(v[u].w)};
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (open[c] && (key[c] & hm) == Pc[c])
+                        atomicAdd(&hist[4 * q + c][hist_slot(radix_digit(key[c], pass))], 1u);
+            }
         }
     }
     __syncthreads();
@@ -662,8 +737,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_split_gram(Side side, Params p,
         __syncthreads();
         const ChunkInfo ci = chunk_info<F>(sp, side, c);
         stage_tile<F>(S.x, S.r, S.idx, side, p.f, ci.lo + ci.start, ci.len);
-        const int sa = ci.slot * F + tid % F;
-        build_masks<F>(S.mask, S.x, ci.len, ci.start, st.P[sa], st.Mk[sa], st.cut[sa]);
+        build_masks<F>(S.mask, S.x, ci.len, ci.start, st.P + ci.slot * F, st.Mk + ci.slot * F, st.cut + ci.slot * F);
         __syncthreads();
         if (masks_out != nullptr)
             for (int e = tid; e < ci.len * W; e += kCtaThreads)

@@ -243,7 +243,7 @@ def gpu_arm(args, p, w, M0, r, rank, world, local_rank):
     return out, eng, (Ru, Ri, tu, tm, tr), dev
 
 
-KERNEL_FAMILIES = ("cta_rows", "warp_rows", "solve_rows", "split_init", "split_hist", "split_scan", "split_eqcount",
+KERNEL_FAMILIES = ("cta_rows", "warp_rows", "solve_rows", "split_init", "split_hist", "split_eqcount",
                    "split_cut", "split_gram", "split_reduce", "sse", "sum_partials")
 
 

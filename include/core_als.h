@@ -79,6 +79,11 @@ extern "C" {
 #define ALS_FP32_TC 3
 
 /* Per-row flags written by the solve. */
+/* refine_steps = ALS_REFINE_AUTO: 0 for ALS_FP32 and ALS_FP32_TC, 1 for
+ * ALS_TF32, 2 for ALS_BF16 - the steps after which a mixed-precision fit
+ * tracks the FP32 one (BF16 rounds to 8 significant bits, TF32 to 11). */
+#define ALS_REFINE_AUTO (-1)
+
 #define ALS_FLAG_RATIO 1     /* pivot ratio above pivot_ratio_max */
 #define ALS_FLAG_SINGULAR 2  /* zero / non-positive pivot: the row was set to 0 */
 #define ALS_FLAG_FP64 4      /* the row was re-assembled and re-solved in FP64 */
@@ -105,7 +110,10 @@ typedef struct als_options {
                                 pivot_ratio_max, or a zero pivot) are
                                 re-assembled from the data and re-solved in
                                 FP64 (flag ALS_FLAG_FP64); 0: off */
-    int refine_steps;        /* iterative-refinement steps after the solve (0 or 1) */
+    int refine_steps;        /* iterative-refinement steps after the solve (0 to 3,
+                                or ALS_REFINE_AUTO): each recomputes the residual
+                                of the FP32 system from the data and solves the
+                                assembled G again (CTA and split rows) */
 } als_options;
 
 typedef struct als_report {
@@ -121,8 +129,8 @@ typedef struct als_report {
 typedef struct als_handle als_handle;
 
 /* Default options: n_f = 32, lambda = 0.05, budget = 0.25, weighted lambda,
- * asymmetric Gram, FP32, pivot_ratio_max = 1e6, FP64 fallback on, no
- * refinement. */
+ * asymmetric Gram, FP32, pivot_ratio_max = 1e6, FP64 fallback on,
+ * refine_steps = ALS_REFINE_AUTO. */
 void als_default_options(als_options* opt_host);
 
 /* Create a handle bound to the current CUDA device and to cuda_stream

@@ -20,8 +20,9 @@ STATUS = {
 }
 ALS_REG_WEIGHTED, ALS_REG_PLAIN = 0, 1
 ALS_GRAM_ASYM, ALS_GRAM_SYM, ALS_GRAM_FULL = 0, 1, 2
-ALS_FP32, ALS_TF32, ALS_BF16 = 0, 1, 2
+ALS_FP32, ALS_TF32, ALS_BF16, ALS_FP32_TC = 0, 1, 2, 3
 ALS_FLAG_RATIO, ALS_FLAG_SINGULAR, ALS_FLAG_FP64 = 1, 2, 4
+ALS_REFINE_AUTO = -1
 ALS_SSE_STATIC_MAX_ENTRIES = 4096 * 16384
 
 

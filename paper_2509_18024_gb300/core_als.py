@@ -54,7 +54,7 @@ class CoreALS:
 
     def __init__(self, n_f: int, lam: float, budget: float, gram_mode: str = "asym",
                  reg_mode: str = "weighted", min_keep: int = 0, ratio_max: float = 1e6,
-                 precision: int = B.ALS_FP32, fp64_fallback: bool = True, refine_steps: int = 0):
+                 precision: int = B.ALS_FP32, fp64_fallback: bool = True, refine_steps: int = B.ALS_REFINE_AUTO):
         _require_cuda()
         self.lib = B.load()
         opt = B.als_options()
@@ -232,7 +232,8 @@ class CoreBatch:
     """
 
     def __init__(self, problems, lam: float, budget: float, gram_mode: str = "asym", reg_mode: str = "weighted",
-                 precision: int = B.ALS_FP32, fp64_fallback: bool = True, refine_steps: int = 0, stream=None):
+                 precision: int = B.ALS_FP32, fp64_fallback: bool = True, refine_steps: int = B.ALS_REFINE_AUTO,
+                 stream=None):
         _require_cuda()
         self.lib = B.load()
         opt = B.als_options()

@@ -66,7 +66,7 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // Layout of Plan::d_split for width F.
 struct SplitLayout {
-    size_t P, Mk, need, cut, done, ghist, eqc, part, total;
+    size_t P, Mk, need, cut, done, ghist, arrive, eqc, part, total;
     SplitLayout(int n_slots, int n_chunks, int F) {
         size_t o = 0;
         const size_t sc = (size_t)std::max(n_slots, 1) * F * 4;
@@ -76,6 +76,7 @@ struct SplitLayout {
         cut = o; o += align256(sc);
         done = o; o += align256(sc);
         ghist = o; o += align256(sc * 256);
+        arrive = o; o += align256((size_t)std::max(n_slots, 1) * 4);
         eqc = o; o += align256((size_t)std::max(n_chunks, 1) * F * 4);
         part = o; o += align256((size_t)std::max(n_chunks, 1) * F * (F + 1) * 4);
         total = o;
@@ -253,7 +254,8 @@ int check_options(als_handle* h, const als_options* o) {
     if (o->min_keep < 0) return set_err(h, ALS_ERR_ARG, "min_keep must be >= 0");
     if (!(o->pivot_ratio_max > 0.0)) return set_err(h, ALS_ERR_ARG, "pivot_ratio_max must be > 0");
     if (o->fp64_fallback != 0 && o->fp64_fallback != 1) return set_err(h, ALS_ERR_ARG, "fp64_fallback must be 0 or 1");
-    if (o->refine_steps < 0 || o->refine_steps > 1) return set_err(h, ALS_ERR_ARG, "refine_steps must be 0 or 1");
+    if (o->refine_steps < ALS_REFINE_AUTO || o->refine_steps > 3)
+        return set_err(h, ALS_ERR_ARG, "refine_steps must be ALS_REFINE_AUTO or 0 to 3");
     return ALS_OK;
 }
 
@@ -373,7 +375,8 @@ int build_plan(als_handle* h, const als_csr* R, Plan** out) {
         return set_err(h, ALS_ERR_OOM, "cudaMalloc(split state, %zu bytes) failed", L.total);
     }
     ALS_CUDA(h, cudaMemcpyAsync(p.d_lists, lists.data(), lists.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    // The split histograms start (and stay between passes) at zero.
+    // The split histograms and arrival counts start (and stay between
+    // passes) at zero.
     ALS_CUDA(h, cudaMemsetAsync(reinterpret_cast<char*>(p.d_split) + L.ghist, 0, L.eqc - L.ghist, st));
     ALS_CUDA(h, cudaStreamSynchronize(st));
     // Keep a small bounded cache of plans.
@@ -463,6 +466,7 @@ int launch_split(als_handle* h, const Plan& pl, const Side& side, const Params& 
     ss.cut = reinterpret_cast<int32_t*>(mem + L.cut);
     ss.done = reinterpret_cast<int32_t*>(mem + L.done);
     ss.ghist = reinterpret_cast<uint32_t*>(mem + L.ghist);
+    ss.arrive = reinterpret_cast<int32_t*>(mem + L.arrive);
     ss.eqc = reinterpret_cast<int32_t*>(mem + L.eqc);
     ss.part = reinterpret_cast<float*>(mem + L.part);
     const int sc = pl.n_slots * F;
@@ -472,7 +476,6 @@ int launch_split(als_handle* h, const Plan& pl, const Side& side, const Params& 
     for (int pass = 0; pass < 4; ++pass) {
         ALS_LAUNCH(h, "split_hist",
                    als::k_split_hist<F><<<pl.n_super, als::kCtaThreads, hsmem, st>>>(side, p, sp, ss, pass));
-        ALS_LAUNCH(h, "split_scan", als::k_split_scan<F><<<(sc * 32 + 255) / 256, 256, 0, st>>>(sp, ss, pass));
     }
     ALS_LAUNCH(h, "split_eqcount", als::k_split_eqcount<F><<<pl.n_chunks, als::kCtaThreads, 0, st>>>(side, p, sp, ss));
     ALS_LAUNCH(h, "split_cut", als::k_split_cut<F><<<(sc * 32 + 255) / 256, 256, 0, st>>>(side, p, sp, ss));
@@ -600,11 +603,12 @@ int run_side(als_handle* h, const Plan& pl, const Side& side, int mode, float* X
         }
     }
     if (refine) {
-        // One refinement step for the CTA and split rows: residual from the
-        // data into the rhs column, second solve of the same G, X += delta.
+        // Refinement steps for the CTA and split rows: residual from the data
+        // into the rhs column, another solve of the same G, X += delta.
         rc = ensure(h, h->delta, (size_t)std::max<int64_t>(pl.n_rows, 1) * p.f * sizeof(float));
         if (rc) return rc;
         float* D = reinterpret_cast<float*>(h->delta.p);
+        for (int step = 0; step < h->opt.refine_steps; ++step)
         for (const Seg& sg : segs) {
             if (sg.count == 0) continue;
             ALS_LAUNCH(h, "refine_resid", als::k_refine_resid<F><<<sg.count, als::kRefineThreads, 0, st>>>(
@@ -697,7 +701,7 @@ void als_default_options(als_options* o) {
     o->precision = ALS_FP32;
     o->pivot_ratio_max = 1e6;
     o->fp64_fallback = 1;
-    o->refine_steps = 0;
+    o->refine_steps = ALS_REFINE_AUTO;
 }
 
 int als_create(als_handle** out, const als_options* opt, void* stream) {
@@ -707,6 +711,8 @@ int als_create(als_handle** out, const als_options* opt, void* stream) {
     if (rc) return rc;
     als_handle* h = new als_handle();
     h->opt = *opt;
+    if (h->opt.refine_steps == ALS_REFINE_AUTO)
+        h->opt.refine_steps = opt->precision == ALS_BF16 ? 2 : (opt->precision == ALS_TF32 ? 1 : 0);
     h->stream = reinterpret_cast<cudaStream_t>(stream);
     if (cudaGetDevice(&h->device) != cudaSuccess) {
         cudaGetLastError();

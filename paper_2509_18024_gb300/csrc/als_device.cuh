@@ -154,7 +154,8 @@ __device__ __forceinline__ void warp_solve(float (&v)[F], float rhs, int f, bool
                                            float& x_lane, int& flags, float& ratio) {
     const int lane = threadIdx.x & 31;
     bool active = lane < F;
-    int ord = -1;  // elimination step at which this lane's row was the pivot
+    int ord = -1;      // elimination step at which this lane's row was the pivot
+    float upiv = 1.f;  // that pivot (the diagonal of the upper factor)
     float pmax = 0.f, pmin = __int_as_float(0x7f800000);
     bool singular = false;
 #pragma unroll
@@ -188,16 +189,19 @@ __device__ __forceinline__ void warp_solve(float (&v)[F], float rhs, int f, bool
         if (lane == bl) {
             active = false;
             ord = k;
+            upiv = pv;
         }
     }
     // Back substitution in pivot order: the row eliminated at step k holds
-    // the k-th row of the upper factor.
+    // the k-th row of the upper factor, whose diagonal is that lane's pivot;
+    // every lane takes the reciprocal of its own pivot at once.
+    const float uinv = 1.0f / upiv;
     float out = 0.f;
 #pragma unroll
     for (int k = F - 1; k >= 0; --k) {
         unsigned owner = __ballot_sync(kFull, ord == k);
         int src = __ffs(owner) - 1;
-        float mine = (ord == k) ? rhs / v[k] : 0.f;
+        float mine = (ord == k) ? rhs * uinv : 0.f;
         float xk = __shfl_sync(kFull, mine, src);
         if (lane == k) out = xk;
         rhs = fmaf(-v[k], xk, rhs);
@@ -245,7 +249,8 @@ __device__ __forceinline__ int hist_slot(int b) { return b + (b >> 5); }
 // Warp-cooperative scan of 256 bins from the top bin down: the bin where the
 // running count first reaches `need` (>= 1; the bins must hold at least
 // `need` keys in total). Padded = shared-memory layout above; otherwise the
-// 256 bins are contiguous. With `zero`, the bins are cleared after reading.
+// 256 bins are contiguous in global memory. With `zero`, the bins are
+// cleared after reading.
 template <bool Padded>
 __device__ __forceinline__ BinPick warp_pick_bin(uint32_t* bins, uint32_t need, bool zero) {
     const int lane = threadIdx.x & 31;
@@ -254,7 +259,9 @@ __device__ __forceinline__ BinPick warp_pick_bin(uint32_t* bins, uint32_t need, 
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const int b = lane * 8 + q;
-        c[q] = bins[Padded ? hist_slot(b) : b];
+        // The contiguous (global) form reads through L2: other CTAs' atomics
+        // made the counts.
+        c[q] = Padded ? bins[hist_slot(b)] : __ldcg(bins + b);
         lsum += c[q];
     }
     if (zero) {

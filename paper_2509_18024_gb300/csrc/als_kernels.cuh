@@ -371,11 +371,24 @@ __global__ void __launch_bounds__(kEvalThreads) k_sse(int64_t n, const int32_t* 
                                                       double* __restrict__ partials) {
     __shared__ double red[kEvalThreads];
     double acc = 0.0;
+    // 16-byte loads when rows are whole float4s (the sum order is a = 0..f-1 either way).
+    const bool vec = (f % 4) == 0 && ((reinterpret_cast<uintptr_t>(U) | reinterpret_cast<uintptr_t>(M)) & 15u) == 0;
     for (int64_t e = blockIdx.x * (int64_t)kEvalThreads + threadIdx.x; e < n; e += (int64_t)gridDim.x * kEvalThreads) {
         const float* u = U + (int64_t)iu[e] * f;
         const float* m = M + (int64_t)im[e] * f;
         float d = 0.f;
-        for (int a = 0; a < f; ++a) d = fmaf(u[a], m[a], d);
+        if (vec) {
+            for (int a = 0; a < f; a += 4) {
+                const float4 x = __ldg(reinterpret_cast<const float4*>(u + a));
+                const float4 y = __ldg(reinterpret_cast<const float4*>(m + a));
+                d = fmaf(x.x, y.x, d);
+                d = fmaf(x.y, y.y, d);
+                d = fmaf(x.z, y.z, d);
+                d = fmaf(x.w, y.w, d);
+            }
+        } else {
+            for (int a = 0; a < f; ++a) d = fmaf(u[a], m[a], d);
+        }
         const double res = (double)r[e] - (double)d;
         acc += res * res;
     }

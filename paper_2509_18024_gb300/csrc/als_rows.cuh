@@ -492,6 +492,7 @@ struct SplitState {  // per (slot, column) selection state and scratch
     int32_t* cut;
     int32_t* done;
     uint32_t* ghist;  // [n_slots][F][256], zero between passes
+    int32_t* arrive;  // [n_slots] super-chunks done with the current pass, zero between passes
     int32_t* eqc;     // [n_chunks][F]
     float* part;      // [n_chunks][F][F+1]
 };
@@ -606,23 +607,30 @@ __global__ void __launch_bounds__(kCtaThreads) k_split_hist(Side side, Params p,
         const uint32_t v = hist[e >> 8][hist_slot(e & 255)];
         if (v) atomicAdd(g + e, v);
     }
-}
-
-// One warp per (slot, column): pick the bin, clear the histogram row.
-template <int F>
-__global__ void k_split_scan(SplitPlan sp, SplitState st, int pass) {
-    const int lane = threadIdx.x & 31;
-    const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (e >= sp.n_slots * F) return;
-    if (st.done[e]) return;
-    uint32_t* bins = st.ghist + (int64_t)e * 256;
-    const BinPick bp = warp_pick_bin<false>(bins, (uint32_t)st.need[e], true);
-    if (lane == 0) {
-        st.P[e] |= (uint32_t)bp.digit << radix_shift(pass);
-        st.Mk[e] = radix_after(pass);
-        st.need[e] = (int)bp.newneed;
-        if (bp.inbin == bp.newneed) st.done[e] = 1;
+    // The super-chunk that finishes the slot's pass last picks the bins of
+    // its open columns (an arrival count; nothing waits). Fences order this
+    // CTA's histogram adds before its arrival, and the arrivals before the
+    // last CTA's reads.
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(st.arrive + slot, 1) == (n + kSplitSuper - 1) / kSplitSuper - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int a = warp; a < F; a += kCtaWarps) {
+        const int e = slot * F + a;
+        if (st.done[e]) continue;
+        const BinPick bp = warp_pick_bin<false>(st.ghist + (int64_t)e * 256, (uint32_t)st.need[e], true);
+        if (lane == 0) {
+            st.P[e] |= (uint32_t)bp.digit << radix_shift(pass);
+            st.Mk[e] = radix_after(pass);
+            st.need[e] = (int)bp.newneed;
+            if (bp.inbin == bp.newneed) st.done[e] = 1;
+        }
     }
+    if (tid == 0) st.arrive[slot] = 0;
 }
 
 // Keys equal to the full threshold key, per chunk and open column.

@@ -66,3 +66,21 @@ def test_option_validation_without_gpu(lib):
     bad.precision = 7
     assert lib.als_create(ctypes.byref(h), ctypes.byref(bad), None) == -1
     assert lib.als_create(None, ctypes.byref(opt), None) == -1
+    bad = B.als_options.from_buffer_copy(opt)
+    bad.refine_steps = 4
+    assert lib.als_create(ctypes.byref(h), ctypes.byref(bad), None) == -1
+    bad.refine_steps = -2
+    assert lib.als_create(ctypes.byref(h), ctypes.byref(bad), None) == -1
+    assert opt.refine_steps == B.ALS_REFINE_AUTO
+
+
+def test_binding_constants_match_the_header():
+    from paper_2509_18024_gb300 import binding as B
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    defines = dict(re.findall(r"#define\s+(ALS_[A-Z0-9_]+)\s+\(?(-?\d+)\)?\s*$", text, flags=re.M))
+    assert len(defines) >= 20
+    for name, value in defines.items():
+        if hasattr(B, name):
+            assert getattr(B, name) == int(value), name
+    for name in ("ALS_FP32", "ALS_TF32", "ALS_BF16", "ALS_FP32_TC", "ALS_REFINE_AUTO", "ALS_FLAG_FP64"):
+        assert int(defines[name]) == getattr(B, name)

@@ -80,12 +80,14 @@ def test_refinement_step_shrinks_mixed_precision_error(core, f, prec):
     lam, r = f32(0.05), 0.25
     Xo, _, _ = oracle.half_sweep(csr.indptr, csr.indices, csr.values, Y.astype(np.float64), lam, r)
     errs = []
-    for steps in (0, 1):
+    for steps in (0, 1, 2):
         eng = core.CoreALS(f, lam, r, precision=prec, refine_steps=steps)
         X = eng.half_sweep(core.DeviceCSR.from_host(csr), torch.as_tensor(Y).cuda()).cpu().numpy()
         errs.append(rel_fro(X, Xo))
-    print(f"f={f} prec={prec} error without / with refinement: {errs[0]:.3e} / {errs[1]:.3e}")
+    print(f"f={f} prec={prec} error after 0 / 1 / 2 refinement steps: {errs[0]:.3e} / {errs[1]:.3e} / {errs[2]:.3e}")
     assert errs[1] <= errs[0] / 10
+    # A second step contracts again until the FP32 solve's own error is reached.
+    assert errs[2] <= max(errs[1] / 4, 2e-6)
 
 
 def test_refinement_keeps_fp32_at_parity(core):

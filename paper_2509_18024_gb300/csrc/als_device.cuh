@@ -18,6 +18,12 @@ enum { FLAG_RATIO = 1, FLAG_SINGULAR = 2, FLAG_FP64 = 4 };
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// Row pitch (floats) of a staged slice tile: n_f plus one float4, so that a
+// warp reading one 4-column quad of 32 consecutive positions as float4 hits
+// all 32 banks once per quarter-warp (a pitch of n_f alone would put every
+// position of a quad in the same four banks).
+__host__ __device__ constexpr int xpitch(int F) { return F + 4; }
+
 struct Params {
     int f;               // rank n_f (<= F, the compile-time padded width)
     float lambda;
@@ -246,31 +252,20 @@ struct BinPick {
 constexpr int kHistRow = 265;
 __device__ __forceinline__ int hist_slot(int b) { return b + (b >> 5); }
 
-// Warp-cooperative scan of 256 bins from the top bin down: the bin where the
-// running count first reaches `need` (>= 1; the bins must hold at least
-// `need` keys in total). Padded = shared-memory layout above; otherwise the
-// 256 bins are contiguous in global memory. With `zero`, the bins are
+// Warp-cooperative scan of 256 contiguous, 16-byte aligned global bins from
+// the top bin down: the bin where the running count first reaches `need`
+// (>= 1; the bins must hold at least `need` keys in total). The bins are
 // cleared after reading.
-template <bool Padded>
-__device__ __forceinline__ BinPick warp_pick_bin(uint32_t* bins, uint32_t need, bool zero) {
+__device__ __forceinline__ BinPick warp_pick_bin(uint32_t* bins, uint32_t need) {
     const int lane = threadIdx.x & 31;
-    uint32_t c[8];
-    uint32_t lsum = 0;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const int b = lane * 8 + q;
-        // The contiguous (global) form reads through L2: other CTAs' atomics
-        // made the counts.
-        c[q] = Padded ? bins[hist_slot(b)] : __ldcg(bins + b);
-        lsum += c[q];
-    }
-    if (zero) {
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int b = lane * 8 + q;
-            bins[Padded ? hist_slot(b) : b] = 0u;
-        }
-    }
+    // Lane l holds bins 8l..8l+7: two 16-byte loads through L2 (other CTAs'
+    // atomics made the counts), then two 16-byte stores of zero.
+    uint4* quad = reinterpret_cast<uint4*>(bins) + 2 * lane;
+    const uint4 lo4 = __ldcg(quad), hi4 = __ldcg(quad + 1);
+    quad[0] = make_uint4(0u, 0u, 0u, 0u);
+    quad[1] = make_uint4(0u, 0u, 0u, 0u);
+    const uint32_t c[8] = {lo4.x, lo4.y, lo4.z, lo4.w, hi4.x, hi4.y, hi4.z, hi4.w};
+    const uint32_t lsum = c[0] + c[1] + c[2] + c[3] + c[4] + c[5] + c[6] + c[7];
     uint32_t incl = lsum;  // keys in bins of lanes >= this lane
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -298,99 +293,6 @@ __device__ __forceinline__ BinPick warp_pick_bin(uint32_t* bins, uint32_t need, 
     r.digit = __shfl_sync(kFull, r.digit, L < 0 ? 0 : L);
     r.newneed = __shfl_sync(kFull, r.newneed, L < 0 ? 0 : L);
     r.inbin = __shfl_sync(kFull, r.inbin, L < 0 ? 0 : L);
-    return r;
-}
-
-// ---------------------------------------------------------------------------
-// 64-bin selection passes (CTA-resident rows). Exponent passes use a window
-// of 63 exponents [T-63, T-1] below an exclusive top T (bins 1..63) plus one
-// bin for everything below (bin 0); mantissa passes take 6 bits at a time
-// (bits 22..17, 16..11, 10..5, 4..0). Bin b of column a sits at
-// a * kHist64Row + b + b / 32: conflict-free both for 32 columns hitting one
-// bin (bank 3a + ...) and for a lane reading bins 2l, 2l + 1.
-constexpr int kHist64Row = 67;
-__device__ __forceinline__ int hist64_slot(int b) { return b + (b >> 5); }
-__device__ __forceinline__ int man_shift(int m) { return m == 0 ? 17 : (m == 1 ? 11 : (m == 2 ? 5 : 0)); }
-__device__ __forceinline__ uint32_t man_before(int m) {
-    return m == 0 ? 0xff800000u : (m == 1 ? 0xfffe0000u : (m == 2 ? 0xfffff800u : 0xffffffe0u));
-}
-__device__ __forceinline__ uint32_t man_after(int m) {
-    return m == 0 ? 0xfffe0000u : (m == 1 ? 0xfffff800u : (m == 2 ? 0xffffffe0u : 0xffffffffu));
-}
-
-// Warp scan of 64 bins from the top (lane l holds bins 2l, 2l + 1), clearing
-// them: the bin where the running count first reaches `need` (>= 1).
-__device__ __forceinline__ BinPick warp_pick_bin64(uint32_t* bins, uint32_t need) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t c0 = bins[hist64_slot(2 * lane)], c1 = bins[hist64_slot(2 * lane + 1)];
-    bins[hist64_slot(2 * lane)] = 0u;
-    bins[hist64_slot(2 * lane + 1)] = 0u;
-    const uint32_t lsum = c0 + c1;
-    uint32_t incl = lsum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_down_sync(kFull, incl, o);
-        if (lane + o < 32) incl += t;
-    }
-    const uint32_t above = incl - lsum;
-    const unsigned ob = __ballot_sync(kFull, above < need && need <= incl);
-    const int L = ob ? __ffs(ob) - 1 : 0;
-    BinPick r;
-    if (above + c1 >= need) {
-        r.digit = 2 * lane + 1;
-        r.newneed = need - above;
-        r.inbin = c1;
-    } else {
-        r.digit = 2 * lane;
-        r.newneed = need - above - c1;
-        r.inbin = c0;
-    }
-    r.digit = __shfl_sync(kFull, r.digit, L);
-    r.newneed = __shfl_sync(kFull, r.newneed, L);
-    r.inbin = __shfl_sync(kFull, r.inbin, L);
-    return r;
-}
-
-// Half-warp form: lanes 0..15 and 16..31 each scan the 64 bins of their own
-// column (lane h of a half holds bins 4h..4h+3) and clear them; `act` false
-// marks an idle half (no column: nothing read or cleared, result unused).
-__device__ __forceinline__ BinPick half_pick_bin64(uint32_t* bins, uint32_t need, bool act) {
-    const int lane = threadIdx.x & 31, h = lane & 15;
-    uint32_t c[4] = {0u, 0u, 0u, 0u};
-    if (act) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            c[q] = bins[hist64_slot(4 * h + q)];
-            bins[hist64_slot(4 * h + q)] = 0u;
-        }
-    }
-    const uint32_t lsum = c[0] + c[1] + c[2] + c[3];
-    uint32_t incl = lsum;
-#pragma unroll
-    for (int o = 1; o < 16; o <<= 1) {
-        const uint32_t t = __shfl_down_sync(kFull, incl, o, 16);
-        if (h + o < 16) incl += t;
-    }
-    const uint32_t above = incl - lsum;
-    const unsigned ob = __ballot_sync(kFull, act && above < need && need <= incl);
-    const unsigned mine = (lane < 16) ? (ob & 0xffffu) : (ob >> 16);
-    const int L = (mine ? __ffs(mine) - 1 : 0) + (lane & 16);
-    BinPick r{0, 0u, 0u};
-    uint32_t cum = above;
-    bool found = false;
-#pragma unroll
-    for (int q = 3; q >= 0; --q) {
-        if (!found && cum + c[q] >= need) {
-            r.digit = 4 * h + q;
-            r.newneed = need - cum;
-            r.inbin = c[q];
-            found = true;
-        }
-        if (!found) cum += c[q];
-    }
-    r.digit = __shfl_sync(kFull, r.digit, L);
-    r.newneed = __shfl_sync(kFull, r.newneed, L);
-    r.inbin = __shfl_sync(kFull, r.inbin, L);
     return r;
 }
 

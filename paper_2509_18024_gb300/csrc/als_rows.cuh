@@ -14,6 +14,7 @@ constexpr int kCtaThreads = 256;
 constexpr int kCtaWarps = kCtaThreads / 32;
 constexpr int kSplitSuper = 4096;  // positions per histogram block of a split row
 constexpr int kGatherBatch = 8;    // independent gathers in flight per thread
+constexpr int kGramBufs = kCtaWarps / 2;  // CUDA-core Gram partial buffers per CTA
 
 // Gram engines: FP32 on CUDA cores (n_f <= 32), or tcgen05 in BF16, TF32,
 // or split TF32 (FP32-accurate).
@@ -51,7 +52,7 @@ struct GramAcc {
     }
     // x: [*][F] row-major tile, mask: keep bits per position (F <= 32: one
     // word), r: ratings.
-    __device__ __forceinline__ void add_tile(const float (*x)[F], const uint32_t* mask, const float* r, int k_begin,
+    __device__ __forceinline__ void add_tile(const float (*x)[xpitch(F)], const uint32_t* mask, const float* r, int k_begin,
                                              int k_end, int k_step, bool sym) {
         const int lane = threadIdx.x & 31;
         const int a0 = (lane >> 2) * TA, b0 = (lane & 3) * TB;
@@ -99,14 +100,16 @@ struct GramAcc {
             }
         }
     }
+    // Gp = this warp's partial (add: Gp += partial).
+    template <bool ADD>
     __device__ __forceinline__ void store(float (*Gp)[F + 1]) const {
         const int lane = threadIdx.x & 31;
         const int a0 = (lane >> 2) * TA, b0 = (lane & 3) * TB;
 #pragma unroll
         for (int q = 0; q < TA; ++q) {
 #pragma unroll
-            for (int t = 0; t < TB; ++t) Gp[a0 + q][b0 + t] = acc[q][t];
-            if ((lane & 3) == 0) Gp[a0 + q][F] = rh[q];
+            for (int t = 0; t < TB; ++t) Gp[a0 + q][b0 + t] = ADD ? Gp[a0 + q][b0 + t] + acc[q][t] : acc[q][t];
+            if ((lane & 3) == 0) Gp[a0 + q][F] = ADD ? Gp[a0 + q][F] + rh[q] : rh[q];
         }
     }
 };
@@ -116,7 +119,7 @@ struct GramAcc {
 // rows (eight threads per 128-byte row at F = 32); else one float each, zero
 // in the padding columns a >= f.
 template <int F>
-__device__ __forceinline__ void stage_tile(float (*x)[F], float* r, int32_t* idx, const Side& side, int f,
+__device__ __forceinline__ void stage_tile(float (*x)[xpitch(F)], float* r, int32_t* idx, const Side& side, int f,
                                            int64_t e0, int cn) {
     for (int k = threadIdx.x; k < cn; k += kCtaThreads) {
         idx[k] = side.indices[e0 + k];
@@ -187,7 +190,7 @@ __device__ __forceinline__ void init_column(int a, int f, long long s, long long
 // neighbouring lanes of that position. pos0 = position of tile row 0 in its
 // row.
 template <int F>
-__device__ __forceinline__ void build_masks(uint32_t (*mask)[MaskWords<F>::value], const float (*x)[F], int cn,
+__device__ __forceinline__ void build_masks(uint32_t (*mask)[MaskWords<F>::value], const float (*x)[xpitch(F)], int cn,
                                             int pos0, const uint32_t* P, const uint32_t* Mk, const int32_t* cut) {
     static_assert(F % 4 == 0 && F / 4 <= 32, "a position's quarters sit in one warp");
     constexpr int T4 = F / 4;                  // threads per position
@@ -225,23 +228,225 @@ __device__ __forceinline__ void build_masks(uint32_t (*mask)[MaskWords<F>::value
 // n_f <= 32). The result (no regulariser) goes to out(a, c, v) for a < F,
 // c <= F, called once per value by some thread. scratch: per-warp partials.
 template <int F, int ENG, class Out>
-__device__ __forceinline__ void gram_tile(uint8_t* scratch, uint64_t*, uint32_t*, const float (*x)[F],
+__device__ __forceinline__ void gram_tile(uint8_t* scratch, uint64_t*, uint32_t*, const float (*x)[xpitch(F)],
                                           const uint32_t (*mask)[MaskWords<F>::value], const float* r, int cn,
                                           bool sym, Out out) {
     static_assert(ENG == ENG_CUDA && F <= 32, "CUDA-core Gram is built for n_f <= 32");
     const int tid = threadIdx.x, warp = tid >> 5;
+    // Warp partials meet in kGramBufs buffers: warps w >= kGramBufs store,
+    // warps w < kGramBufs add theirs into buffer w, then the buffers are summed.
     float (*Gp)[F][F + 1] = reinterpret_cast<float (*)[F][F + 1]>(scratch);
     GramAcc<F> g;
     g.zero();
     g.add_tile(x, &mask[0][0], r, warp, cn, kCtaWarps, sym);
-    g.store(Gp[warp]);
+    if (warp >= kGramBufs) g.template store<false>(Gp[warp - kGramBufs]);
+    __syncthreads();
+    if (warp < kGramBufs) g.template store<true>(Gp[warp]);
     __syncthreads();
     for (int e = tid; e < F * (F + 1); e += kCtaThreads) {
         const int a = e / (F + 1), c = e % (F + 1);
         float v = 0.f;
 #pragma unroll
-        for (int q = 0; q < kCtaWarps; ++q) v += Gp[q][a][c];
+        for (int q = 0; q < kGramBufs; ++q) v += Gp[q][a][c];
         out(a, c, v);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// CES of a resident slice, one warp per quad of 4 columns (Algorithm 1 per
+// column: the s largest |x_ka|, ties to the lower position), by an exact
+// radix select on the magnitude keys with 64 bins per column and pass:
+//   window pass: keys whose exponent E lies in [T - 16, T) go to bin
+//     ((E - T + 16) << 2) | key bits 22..21 (quarter octaves). T starts one
+//     above the column's largest exponent; if the window holds fewer than
+//     `need` keys, they are all kept and the window moves down (T -= 16).
+//   mantissa passes: key bits 20..15, 14..9, 8..3, 2..0 of the keys equal to
+//     the prefix P on the bits resolved so far (mask Mk).
+// A column is done when the bin holding the need-th key is taken whole;
+// keys equal to P on all 31 bits beyond that are cut by position. Bins of
+// one column: 64 counts at b + 4 (b / 32) (16-byte aligned octets, read as
+// two uint4 by the 8 lanes scanning that column).
+constexpr int kQuadPitch = 72;
+constexpr int kQuadHistWords = 4 * kQuadPitch;
+__device__ __forceinline__ int mpass_shift(int m) { return m == 0 ? 15 : (m == 1 ? 9 : (m == 2 ? 3 : 0)); }
+__device__ __forceinline__ uint32_t mpass_digits(int m) { return m == 3 ? 7u : 63u; }
+__device__ __forceinline__ uint32_t mpass_after(int m) {
+    return m == 0 ? 0xffff8000u : (m == 1 ? 0xfffffe00u : (m == 2 ? 0xfffffff8u : 0xffffffffu));
+}
+
+// Scan of the 4 columns' bins of one pass: lanes 8c..8c+7 scan column c (lane
+// 8c + g holds bins 8g..8g+7) from the top bin down, clear what they read,
+// and return (in every lane of the group) the packed outcome: bit 0 found,
+// bit 1 the bin is taken whole, bits 2..7 the bin, bits 8..19 the keys still
+// needed inside it - or, when the bins hold fewer than `need` keys, found = 0
+// and bits 8..19 = need minus the keys binned.
+__device__ __forceinline__ uint32_t quad_scan(uint32_t* H, bool act, uint32_t need) {
+    const int lane = threadIdx.x & 31, g = lane & 7, c = lane >> 3;
+    uint4* oct = reinterpret_cast<uint4*>(H + c * kQuadPitch + 8 * g + ((g >> 2) << 2));
+    uint4 lo4 = make_uint4(0u, 0u, 0u, 0u), hi4 = lo4;
+    if (act) {
+        lo4 = oct[0];
+        hi4 = oct[1];
+        oct[0] = make_uint4(0u, 0u, 0u, 0u);
+        oct[1] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    const uint32_t b[8] = {lo4.x, lo4.y, lo4.z, lo4.w, hi4.x, hi4.y, hi4.z, hi4.w};
+    const uint32_t lsum = b[0] + b[1] + b[2] + b[3] + b[4] + b[5] + b[6] + b[7];
+    uint32_t incl = lsum;  // keys in bins >= 8g of this column
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+        const uint32_t t = __shfl_down_sync(kFull, incl, o, 8);
+        if (g + o < 8) incl += t;
+    }
+    const uint32_t above = incl - lsum;
+    const bool here = act && above < need && need <= incl;
+    const unsigned grp = (__ballot_sync(kFull, here) >> (8 * c)) & 0xffu;
+    const uint32_t total = __shfl_sync(kFull, incl, lane & ~7);
+    uint32_t out = 0u;
+    if (here) {
+        uint32_t cum = above;
+        bool found = false;
+#pragma unroll
+        for (int q = 7; q >= 0; --q) {
+            if (!found && cum + b[q] >= need) {
+                const uint32_t nn = need - cum;
+                out = 1u | ((b[q] == nn) ? 2u : 0u) | ((uint32_t)(8 * g + q) << 2) | (nn << 8);
+                found = true;
+            }
+            if (!found) cum += b[q];
+        }
+    }
+    out = __shfl_sync(kFull, out, (lane & ~7) + (grp ? __ffs(grp) - 1 : 0));
+    if (!grp) out = (need - total) << 8;
+    return out;
+}
+
+// Warp-level CES of columns 4q..4q+3 of a staged slice (n <= 4095
+// positions): writes their keep rule (P, Mk, cut). H: this warp's
+// kQuadHistWords bins, all zero on entry and on return.
+template <int F>
+__device__ __forceinline__ void quad_select(const float (*x)[xpitch(F)], int n, int f, long long s, int q, uint32_t* H,
+                                            uint32_t* P_out, uint32_t* Mk_out, int32_t* cut_out) {
+    const int lane = threadIdx.x & 31;
+    uint32_t P[4], Mk[4];
+    int need[4], cut[4], T[4];
+    bool open[4], wres[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        int done;
+        init_column(4 * q + c, f, s, n, P[c], Mk[c], need[c], cut[c], done);
+        open[c] = !done;
+        wres[c] = false;
+    }
+    const float4* xq = reinterpret_cast<const float4*>(&x[0][4 * q]);
+    constexpr int XQ = xpitch(F) / 4;  // float4 per tile row
+    if (open[0] || open[1] || open[2] || open[3]) {
+        uint32_t em[4] = {0u, 0u, 0u, 0u};
+        for (int k = lane; k < n; k += 32) {
+            const float4 v = xq[k * XQ];
+            em[0] = max(em[0], mag_key(v.x) >> 23);
+            em[1] = max(em[1], mag_key(v.y) >> 23);
+            em[2] = max(em[2], mag_key(v.z) >> 23);
+            em[3] = max(em[3], mag_key(v.w) >> 23);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) T[c] = (int)__reduce_max_sync(kFull, em[c]) + 1;
+    }
+    // Bin b (< 64) of column c sits at word c * kQuadPitch + b + ((b >> 3) & 4).
+    // Window passes (at most 16 windows of 16 exponents cover all 256).
+    for (int it = 0; it < 16; ++it) {
+        bool act[4];
+        uint32_t tlo[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            act[c] = open[c] && !wres[c];
+            tlo[c] = (uint32_t)(T[c] - 16);
+        }
+        if (!(act[0] || act[1] || act[2] || act[3])) break;
+        for (int k = lane; k < n; k += 32) {
+            const float4 v = xq[k * XQ];
+            const uint32_t key[4] = {mag_key(v.x), mag_key(v.y), mag_key(v.z), mag_key(v.w)};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const uint32_t d = (key[c] >> 23) - tlo[c];  // window row, >= 16 outside
+                const uint32_t b = (d << 2) | ((key[c] >> 21) & 3u);
+                if (act[c] && d < 16u) atomicAdd(H + c * kQuadPitch + b + ((b >> 3) & 4u), 1u);
+            }
+        }
+        __syncwarp();
+        const int cs = lane >> 3;
+        const uint32_t res = quad_scan(H, cs == 0 ? act[0] : cs == 1 ? act[1] : cs == 2 ? act[2] : act[3],
+                                       (uint32_t)(cs == 0 ? need[0] : cs == 1 ? need[1] : cs == 2 ? need[2] : need[3]));
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const uint32_t rc = __shfl_sync(kFull, res, 8 * c);
+            if (!act[c]) continue;
+            if (rc & 1u) {
+                const uint32_t dg = (rc >> 2) & 63u;
+                P[c] = ((uint32_t)(T[c] - 16 + (int)(dg >> 2)) << 23) | ((dg & 3u) << 21);
+                Mk[c] = 0xffe00000u;
+                need[c] = (int)(rc >> 8);
+                wres[c] = true;
+                if (rc & 2u) open[c] = false;
+            } else {
+                need[c] = (int)(rc >> 8);  // the window's keys are all kept
+                T[c] -= 16;
+            }
+        }
+        __syncwarp();
+    }
+    // Mantissa passes.
+    for (int m = 0; m < 4; ++m) {
+        if (!(open[0] || open[1] || open[2] || open[3])) break;
+        const int sh = mpass_shift(m);
+        const uint32_t dm = mpass_digits(m);
+        for (int k = lane; k < n; k += 32) {
+            const float4 v = xq[k * XQ];
+            const uint32_t key[4] = {mag_key(v.x), mag_key(v.y), mag_key(v.z), mag_key(v.w)};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const uint32_t b = (key[c] >> sh) & dm;
+                if (open[c] && (key[c] & Mk[c]) == P[c]) atomicAdd(H + c * kQuadPitch + b + ((b >> 3) & 4u), 1u);
+            }
+        }
+        __syncwarp();
+        const int cs = lane >> 3;
+        const uint32_t res = quad_scan(H, cs == 0 ? open[0] : cs == 1 ? open[1] : cs == 2 ? open[2] : open[3],
+                                       (uint32_t)(cs == 0 ? need[0] : cs == 1 ? need[1] : cs == 2 ? need[2] : need[3]));
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const uint32_t rc = __shfl_sync(kFull, res, 8 * c);
+            if (!open[c]) continue;
+            P[c] |= ((rc >> 2) & 63u) << sh;
+            Mk[c] = mpass_after(m);
+            need[c] = (int)(rc >> 8);
+            if (rc & 2u) open[c] = false;
+        }
+        __syncwarp();
+    }
+    // Columns still open: the full key P has more copies than places left;
+    // keep the lowest positions.
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        if (!open[c]) continue;
+        int seen = 0;
+        for (int kb = 0; kb < n; kb += 32) {
+            const int k = kb + lane;
+            unsigned bl = __ballot_sync(kFull, k < n && mag_key(x[k][4 * q + c]) == P[c]);
+            const int cnt = __popc(bl);
+            if (seen + cnt >= need[c]) {
+                for (int want = need[c] - seen; --want > 0;) bl &= bl - 1u;
+                cut[c] = kb + __ffs(bl);
+                break;
+            }
+            seen += cnt;
+        }
+    }
+    if (lane < 4) {
+        const int c = lane;
+        P_out[4 * q + c] = c == 0 ? P[0] : c == 1 ? P[1] : c == 2 ? P[2] : P[3];
+        Mk_out[4 * q + c] = c == 0 ? Mk[0] : c == 1 ? Mk[1] : c == 2 ? Mk[2] : Mk[3];
+        cut_out[4 * q + c] = c == 0 ? cut[0] : c == 1 ? cut[1] : c == 2 ? cut[2] : cut[3];
     }
 }
 
@@ -256,25 +461,20 @@ struct TileBytes {
 template <int F, int NS, int ENG>
 struct CtaSmem {
     static constexpr int W = MaskWords<F>::value;
-    static constexpr int HIST_BYTES = F * kHist64Row * 4;
-    static constexpr int GRAM_BYTES = ENG == ENG_CUDA ? kCtaWarps * F * (F + 1) * 4 : 0;
+    static constexpr int HIST_BYTES = kCtaWarps * kQuadHistWords * 4;
+    static constexpr int GRAM_BYTES = ENG == ENG_CUDA ? kGramBufs * F * (F + 1) * 4 : 0;
     static constexpr int U_BYTES = HIST_BYTES > GRAM_BYTES ? HIST_BYTES : GRAM_BYTES;
-    float x[NS][F];
+    float x[NS][xpitch(F)];
     float r[NS];
     int32_t idx[NS];
     uint32_t mask[NS][W];
-    __align__(1024) uint8_t u[U_BYTES];  // histograms (then CUDA-core Gram partials)
+    __align__(1024) uint8_t u[U_BYTES];  // per-warp selection bins (then CUDA-core Gram partials)
     __align__(1024) uint8_t tiles[TileBytes<F, ENG>::value];  // tensor-core operands
     uint64_t bars[2];
     uint32_t tmem_slot;
     uint32_t P[F];
     uint32_t Mk[F];
-    int32_t need[F];
     int32_t cut[F];
-    int32_t done[F];
-    int32_t eres[F];   // exponent of the threshold resolved
-    uint32_t wtop[F];  // exclusive exponent top of the next window pass
-    __device__ uint32_t (*hist())[kHist64Row] { return reinterpret_cast<uint32_t (*)[kHist64Row]>(u); }
 };
 
 // mode 0/1: write the augmented system of list entry w to G_aug[w]; mode 2:
@@ -283,7 +483,7 @@ struct CtaSmem {
 // once per CTA, and each row's accumulator is read back after the next row
 // has been staged and selected (its MMAs run meanwhile).
 template <int F, int NS, int ENG>
-__global__ void __launch_bounds__(kCtaThreads) k_cta_rows(Side side, Params p, const int32_t* __restrict__ rows,
+__global__ void __launch_bounds__(kCtaThreads, ENG == ENG_CUDA ? 4 : 1) k_cta_rows(Side side, Params p, const int32_t* __restrict__ rows,
                                                           int n_list, int mode, float* __restrict__ G_aug,
                                                           uint32_t* __restrict__ masks_out) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -318,128 +518,14 @@ __global__ void __launch_bounds__(kCtaThreads) k_cta_rows(Side side, Params p, c
     const int64_t lo = side.indptr[i];
     const int n = (int)(side.indptr[i + 1] - lo);
     const long long s = row_budget(n, p);
-    const int a_t = tid % F;  // thread t always handles column t mod F
-    const int k0 = tid / F;
-    constexpr int kstep = kCtaThreads / F;
-    static_assert(F % kCtaWarps == 0, "the bin scans give each warp F / kCtaWarps columns");
-    uint32_t (*hist)[kHist64Row] = S.hist();
-
-    if (tid < F) {
-        uint32_t P, Mk;
-        int need, cut, done;
-        init_column(tid, f, s, n, P, Mk, need, cut, done);
-        S.P[tid] = P;
-        S.Mk[tid] = Mk;
-        S.need[tid] = need;
-        S.cut[tid] = cut;
-        S.done[tid] = done;
-        S.eres[tid] = 0;
-        S.wtop[tid] = 0u;
-    }
-    // Histograms start at zero; each scan re-zeroes the bins it read.
-    for (int e = tid; e < F * kHist64Row; e += kCtaThreads) (&hist[0][0])[e] = 0u;
     stage_tile<F>(S.x, S.r, S.idx, side, f, lo, n);
+    // CES: warp w selects the column quads w, w + 8, ... on its own bins
+    // (cleared first: the CUDA-core Gram of the previous row reused them).
     {
-        // Window top of each column: its largest exponent + 1.
-        if (!S.done[a_t]) {
-            uint32_t em = 0u;
-            for (int k = k0; k < n; k += kstep) em = max(em, mag_key(S.x[k][a_t]) >> 23);
-            atomicMax(&S.wtop[a_t], em + 1u);
-        }
-    }
-    __syncthreads();
-
-    // Exponent of the s-th largest key: windows of 63 exponents from the top.
-    bool more = __syncthreads_or(!S.done[a_t] && !S.eres[a_t]);
-    for (int it = 0; it < 5 && more; ++it) {
-        if (!S.done[a_t] && !S.eres[a_t]) {
-            const int T = (int)S.wtop[a_t];
-            for (int k = k0; k < n; k += kstep) {
-                const int E = (int)(mag_key(S.x[k][a_t]) >> 23);
-                if (E < T) atomicAdd(&hist[a_t][hist64_slot(E >= T - 63 ? E - T + 64 : 0)], 1u);
-            }
-        }
-        __syncthreads();
-        // Two columns per warp scan (a half-warp each).
-        for (int j = 0; j < F / kCtaWarps; j += 2) {
-            const int ca = warp + kCtaWarps * j;
-            const int cb = (j + 1 < F / kCtaWarps) ? ca + kCtaWarps : -1;
-            const int a = (lane < 16) ? ca : cb;
-            const bool act = a >= 0 && !S.done[a] && !S.eres[a];
-            if (!__any_sync(kFull, act)) continue;
-            const BinPick bp = half_pick_bin64(hist[act ? a : ca], act ? (uint32_t)S.need[a] : 0u, act);
-            if ((lane & 15) == 0 && act) {
-                const int T = (int)S.wtop[a];
-                if (bp.digit >= 1) {
-                    S.P[a] = (uint32_t)(T - 64 + bp.digit) << 23;
-                    S.Mk[a] = 0xff800000u;
-                    S.need[a] = (int)bp.newneed;
-                    S.eres[a] = 1;
-                    if (bp.inbin == bp.newneed) S.done[a] = 1;
-                } else if (bp.inbin == bp.newneed) {
-                    S.P[a] = 0u;  // everything below the window is kept too: keep all
-                    S.Mk[a] = 0u;
-                    S.done[a] = 1;
-                } else {
-                    S.wtop[a] = (uint32_t)(T - 63);
-                    S.need[a] = (int)bp.newneed;
-                }
-            }
-        }
-        __syncthreads();
-        more = __syncthreads_or(!S.done[a_t] && !S.eres[a_t]);
-    }
-    // Mantissa, 6 bits per pass, inside the resolved exponent.
-    more = __syncthreads_or(!S.done[a_t]);
-    for (int m = 0; m < 4 && more; ++m) {
-        const uint32_t hm = man_before(m);
-        const int sh = man_shift(m);
-        if (!S.done[a_t]) {
-            const uint32_t Pa = S.P[a_t];
-            for (int k = k0; k < n; k += kstep) {
-                const uint32_t key = mag_key(S.x[k][a_t]);
-                if ((key & hm) == Pa) atomicAdd(&hist[a_t][hist64_slot((key >> sh) & 63u)], 1u);
-            }
-        }
-        __syncthreads();
-        for (int j = 0; j < F / kCtaWarps; j += 2) {
-            const int ca = warp + kCtaWarps * j;
-            const int cb = (j + 1 < F / kCtaWarps) ? ca + kCtaWarps : -1;
-            const int a = (lane < 16) ? ca : cb;
-            const bool act = a >= 0 && !S.done[a];
-            if (!__any_sync(kFull, act)) continue;
-            const BinPick bp = half_pick_bin64(hist[act ? a : ca], act ? (uint32_t)S.need[a] : 0u, act);
-            if ((lane & 15) == 0 && act) {
-                S.P[a] |= (uint32_t)bp.digit << sh;
-                S.Mk[a] = man_after(m);
-                S.need[a] = (int)bp.newneed;
-                if (bp.inbin == bp.newneed) S.done[a] = 1;
-            }
-        }
-        __syncthreads();
-        more = __syncthreads_or(!S.done[a_t]);
-    }
-    // Open columns: the full key P has more copies than places left; keep the
-    // lowest positions.
-    for (int a = warp; a < F; a += kCtaWarps) {
-        if (S.done[a]) continue;
-        const uint32_t T = S.P[a];
-        const int nd = S.need[a];
-        int seen = 0, cut = n;
-        for (int kb = 0; kb < n; kb += 32) {
-            const int k = kb + lane;
-            const bool eq = k < n && mag_key(S.x[k][a]) == T;
-            unsigned b = __ballot_sync(kFull, eq);
-            const int c = __popc(b);
-            if (seen + c >= nd) {
-                int want = nd - seen;
-                while (--want > 0) b &= b - 1u;
-                cut = kb + __ffs(b);
-                break;
-            }
-            seen += c;
-        }
-        if (lane == 0) S.cut[a] = cut;
+        uint32_t* H = reinterpret_cast<uint32_t*>(S.u) + warp * kQuadHistWords;
+        for (int e = lane; e < kQuadHistWords / 4; e += 32) reinterpret_cast<uint4*>(H)[e] = make_uint4(0u, 0u, 0u, 0u);
+        __syncwarp();
+        for (int q = warp; q < F / 4; q += kCtaWarps) quad_select<F>(S.x, n, f, s, q, H, S.P, S.Mk, S.cut);
     }
     __syncthreads();
     build_masks<F>(S.mask, S.x, n, 0, S.P, S.Mk, S.cut);
@@ -595,9 +681,10 @@ __global__ void __launch_bounds__(kCtaThreads) k_split_hist(Side side, Params p,
                 if (j[u] < 0) continue;
                 const uint32_t key[4] = {mag_key(v[u].x), mag_key(v[u].y), mag_key(v[u].z), mag_key(v[u].w)};
 #pragma unroll
-                for (int c = 0; c < 4; ++c)
+                for (int c = 0; c < 4; ++c) {
                     if (open[c] && (key[c] & hm) == Pc[c])
                         atomicAdd(&hist[4 * q + c][hist_slot(radix_digit(key[c], pass))], 1u);
+                }
             }
         }
     }
@@ -622,7 +709,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_split_hist(Side side, Params p,
     for (int a = warp; a < F; a += kCtaWarps) {
         const int e = slot * F + a;
         if (st.done[e]) continue;
-        const BinPick bp = warp_pick_bin<false>(st.ghist + (int64_t)e * 256, (uint32_t)st.need[e], true);
+        const BinPick bp = warp_pick_bin(st.ghist + (int64_t)e * 256, (uint32_t)st.need[e]);
         if (lane == 0) {
             st.P[e] |= (uint32_t)bp.digit << radix_shift(pass);
             st.Mk[e] = radix_after(pass);
@@ -704,11 +791,11 @@ template <int F, int ENG>
 struct SplitGramSmem {
     static constexpr int CH = SplitChunk<F>::value;
     static constexpr int W = MaskWords<F>::value;
-    float x[CH][F];
+    float x[CH][xpitch(F)];
     float r[CH];
     int32_t idx[CH];
     uint32_t mask[CH][W];
-    __align__(1024) uint8_t u[ENG == ENG_CUDA ? kCtaWarps * F * (F + 1) * 4 : 16];
+    __align__(1024) uint8_t u[ENG == ENG_CUDA ? kGramBufs * F * (F + 1) * 4 : 16];
     __align__(1024) uint8_t tiles[TileBytes<F, ENG>::value];
     uint64_t bars[2];
     uint32_t tmem_slot;

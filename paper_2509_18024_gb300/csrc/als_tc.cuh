@@ -176,7 +176,7 @@ __device__ __forceinline__ void tc_pipe_drain(TcPipe& P, uint64_t* bars, int b) 
 // Accumulate positions [0, n) of a staged tile into accumulator `acc`
 // (0 or 1), starting it from zero. All threads call it; MMAs stay in flight.
 template <int F, int PREC, int W>
-__device__ __forceinline__ void tc_pipe_row(TcPipe& P, uint8_t* tiles, uint64_t* bars, const float (*x)[F],
+__device__ __forceinline__ void tc_pipe_row(TcPipe& P, uint8_t* tiles, uint64_t* bars, const float (*x)[xpitch(F)],
                                             const uint32_t (*mask)[W], const float* r, int n, bool sym, int acc) {
     using C = TcCfg<F, PREC>;
     const int tid = threadIdx.x;

@@ -43,6 +43,8 @@ struct Plan {
     int n_bucket[3] = {0, 0, 0};
     int n_slots = 0, n_chunks = 0, n_super = 0;
     int64_t max_len = 0;
+    std::vector<int64_t> host_indptr;  // the indptr the plan was built from
+    bool stale = false;                // the buffers were refilled: re-check before use
     int32_t* d_lists = nullptr;  // [warp | bucket0 | bucket1 | bucket2 | split rows | c_begin | ch_slot | ch_start
                                  //  | sc_slot | sc_start]
     void* d_split = nullptr;     // split-row selection state and scratch
@@ -283,24 +285,16 @@ double* eval_out(als_handle* h) { return eval_partials(h) + als::kEvalBlocks; }
 unsigned* valid_err(als_handle* h) { return reinterpret_cast<unsigned*>(eval_out(h) + 1); }
 constexpr size_t kMiscBytes = 256 + (als::kEvalBlocks + 1) * sizeof(double) + 64;
 
-int build_plan(als_handle* h, const als_csr* R, Plan** out) {
-    for (auto& p : h->plans) {
-        if (p.indptr == R->indptr && p.n_rows == R->n_rows && p.nnz == R->nnz && p.n_cols == R->n_cols &&
-            p.tuning.split_at_middle == h->tuning.split_at_middle && p.tuning.warp_rows == h->tuning.warp_rows &&
-            p.tuning.tc_gram == h->tuning.tc_gram) {
-            *out = &p;
-            return ALS_OK;
-        }
-    }
-    // Validate the structure on the device, then plan on the host.
+// Validate one side's structure on the device and download its indptr.
+int validate_csr(als_handle* h, const als_csr* R, std::vector<int64_t>& indptr) {
     cudaStream_t st = h->stream;
     ALS_CUDA(h, cudaMemsetAsync(valid_err(h), 0, sizeof(unsigned), st));
     if (R->n_rows > 0) {
-        int blocks = (int)std::min<int64_t>((R->n_rows + 255) / 256, 4096);
+        int blocks = (int)std::min<int64_t>((std::max(R->n_rows, R->nnz) + 255) / 256, (int64_t)h->n_sm * 8);
         ALS_LAUNCH(h, "validate", als::k_validate<<<blocks, 256, 0, st>>>(R->indptr, R->indices, R->values, R->n_rows, R->n_cols, R->nnz,
                                                 valid_err(h)));
     }
-    std::vector<int64_t> indptr(R->n_rows + 1);
+    indptr.resize(R->n_rows + 1);
     unsigned err = 0;
     ALS_CUDA(h, cudaMemcpyAsync(indptr.data(), R->indptr, sizeof(int64_t) * (R->n_rows + 1), cudaMemcpyDeviceToHost, st));
     ALS_CUDA(h, cudaMemcpyAsync(&err, valid_err(h), sizeof(unsigned), cudaMemcpyDeviceToHost, st));
@@ -309,6 +303,45 @@ int build_plan(als_handle* h, const als_csr* R, Plan** out) {
     if (err & 1u) return set_err(h, ALS_ERR_CSR, "indptr is not monotone from 0 to nnz");
     if (err & 2u) return set_err(h, ALS_ERR_CSR, "indices out of range, unsorted or duplicated inside a row");
     if (err & 4u) return set_err(h, ALS_ERR_NONFINITE, "non-finite rating value");
+    return ALS_OK;
+}
+
+int build_plan(als_handle* h, const als_csr* R, Plan** out) {
+    std::vector<int64_t> indptr;
+    bool checked = false;
+    for (size_t q = 0; q < h->plans.size(); ++q) {
+        Plan& p = h->plans[q];
+        if (p.indptr == R->indptr && p.n_rows == R->n_rows && p.nnz == R->nnz && p.n_cols == R->n_cols &&
+            p.tuning.split_at_middle == h->tuning.split_at_middle && p.tuning.warp_rows == h->tuning.warp_rows &&
+            p.tuning.tc_gram == h->tuning.tc_gram) {
+            if (!p.stale) {
+                *out = &p;
+                return ALS_OK;
+            }
+            // The buffers were refilled: validate the new contents; the plan
+            // stands if the row structure (indptr) is unchanged.
+            int rc = validate_csr(h, R, indptr);
+            if (rc) return rc;
+            checked = true;
+            if (indptr == p.host_indptr) {
+                // Histograms and arrival counts start from zero again (a
+                // failed call may have left them dirty).
+                const SplitLayout L(p.n_slots, p.n_chunks, p.F);
+                ALS_CUDA(h, cudaMemsetAsync(reinterpret_cast<char*>(p.d_split) + L.ghist, 0, L.eqc - L.ghist, h->stream));
+                p.stale = false;
+                *out = &p;
+                return ALS_OK;
+            }
+            free_plan(p);
+            h->plans.erase(h->plans.begin() + q);
+            break;
+        }
+    }
+    if (!checked) {
+        int rc = validate_csr(h, R, indptr);
+        if (rc) return rc;
+    }
+    cudaStream_t st = h->stream;
 
     const int F = plan_width(h);
     const BucketCaps caps = bucket_caps(F);
@@ -354,6 +387,7 @@ int build_plan(als_handle* h, const als_csr* R, Plan** out) {
     p.n_chunks = (int)ch_slot.size();
     p.n_super = (int)sc_slot.size();
     p.max_len = max_len;
+    p.host_indptr = indptr;
     std::vector<int32_t> lists(warp_rows);
     for (auto& v : bucket) lists.insert(lists.end(), v.begin(), v.end());
     lists.insert(lists.end(), split_rows.begin(), split_rows.end());
@@ -1019,20 +1053,15 @@ int als_fit_host(als_handle* h, int64_t n_u, int64_t n_m, int64_t nnz, const int
     ALS_CUDA(h, cudaMemcpyAsync(U_host, d_U, n_u * f * 4, cudaMemcpyDeviceToHost, st));
     ALS_CUDA(h, cudaMemcpyAsync(M_host, d_M, n_m * f * 4, cudaMemcpyDeviceToHost, st));
     ALS_CUDA(h, cudaStreamSynchronize(st));
-    // The device copies of the structure are reused by later calls only if
-    // they hold the same data, which this call cannot know: drop their plans
-    // and the captured sweep.
+    // The next call refills these device buffers: its plans must re-check
+    // the contents (kept when the row structure is unchanged), and the
+    // captured sweep is dropped.
     if (h->fit_graph.exec) {
         cudaGraphExecDestroy(h->fit_graph.exec);
         h->fit_graph = {};
     }
-    h->plans.erase(std::remove_if(h->plans.begin(), h->plans.end(),
-                                  [&](const Plan& p) {
-                                      bool mine = p.indptr == d_uip || p.indptr == d_iip;
-                                      if (mine) free_plan(const_cast<Plan&>(p));
-                                      return mine;
-                                  }),
-                   h->plans.end());
+    for (Plan& p : h->plans)
+        if (p.indptr == d_uip || p.indptr == d_iip) p.stale = true;
     return ALS_OK;
 }
 

@@ -336,27 +336,34 @@ __global__ void k_unpack_aug(const float* __restrict__ G_aug, const int32_t* __r
 // Structure check of one side: indptr monotone from 0 to nnz, indices in
 // range and strictly increasing inside each row, values finite.
 // err bits: 1 = indptr, 2 = index range/order, 4 = non-finite value.
+// Entry-parallel: an entry whose index does not exceed its predecessor's must
+// start a row, which a binary search of indptr decides (bounded by log2 of
+// the row count even when indptr itself is malformed).
 __global__ void k_validate(const int64_t* __restrict__ indptr, const int32_t* __restrict__ indices,
                            const float* __restrict__ values, int64_t n_rows, int64_t n_cols, int64_t nnz,
                            unsigned* err) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_rows; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    unsigned bad = 0u;
+    for (int64_t i = t0; i < n_rows; i += stride) {
         const int64_t a = indptr[i], b = indptr[i + 1];
-        if (a < 0 || b < a || b > nnz || (i == 0 && a != 0) || (i == n_rows - 1 && b != nnz)) {
-            atomicOr(err, 1u);
-            continue;
-        }
-        int32_t prev = -1;
-        for (int64_t e = a; e < b; ++e) {
-            const int32_t j = indices[e];
-            if (j <= prev || j >= n_cols) {
-                atomicOr(err, 2u);
-                break;
+        if (a < 0 || b < a || b > nnz || (i == 0 && a != 0) || (i == n_rows - 1 && b != nnz)) bad |= 1u;
+    }
+    for (int64_t e = t0; e < nnz; e += stride) {
+        const int32_t j = indices[e];
+        if (j < 0 || j >= n_cols) bad |= 2u;
+        if (!(fabsf(values[e]) <= 3.402823466e38f)) bad |= 4u;
+        if (e > 0 && j <= indices[e - 1]) {
+            int64_t lo = 0, hi = n_rows;  // first i with indptr[i] >= e
+            for (int it = 0; it < 64 && lo < hi; ++it) {
+                const int64_t mid = lo + (hi - lo) / 2;
+                if (indptr[mid] < e) lo = mid + 1;
+                else hi = mid;
             }
-            prev = j;
-            const float v = values[e];
-            if (!(fabsf(v) <= 3.402823466e38f)) atomicOr(err, 4u);
+            if (indptr[lo] != e) bad |= 2u;
         }
     }
+    if (bad) atomicOr(err, bad);
 }
 
 // ---------------------------------------------------------------------------

@@ -574,7 +574,8 @@ int run_side(als_handle* h, const Plan& pl, const Side& side, int mode, float* X
              uint32_t* masks_out, float* G_out, float* b_out) {
     cudaStream_t st = h->stream;
     Params p = make_params(h->opt);
-    const int n_aug = std::max(pl.n_cta_like(), mode == 1 ? pl.n_warp : 0);
+    const int n_warp = F <= 32 ? pl.n_warp : 0;
+    const int n_aug = n_warp + pl.n_cta_like();
     int rc = ensure(h, h->g_aug, (size_t)std::max(n_aug, 1) * F * (F + 1) * sizeof(float));
     if (rc) return rc;
     float* G_aug = reinterpret_cast<float*>(h->g_aug.p);
@@ -594,11 +595,14 @@ int run_side(als_handle* h, const Plan& pl, const Side& side, int mode, float* X
             fb.count = &counters(h)->fb_count;
         }
     }
-    // Augmented systems: [split slots | bucket0 | bucket1 | bucket2] in G_aug.
-    float* aug_split = G_aug;
-    float* aug_b0 = aug_split + (size_t)pl.n_slots * F * (F + 1);
-    float* aug_b1 = aug_b0 + (size_t)pl.n_bucket[0] * F * (F + 1);
-    float* aug_b2 = aug_b1 + (size_t)pl.n_bucket[1] * F * (F + 1);
+    // Augmented systems in row-list order: [warp rows | bucket0 | bucket1 |
+    // bucket2 | split slots], so that one batched solve covers all rows.
+    constexpr size_t FF = (size_t)F * (F + 1);
+    float* aug_warp = G_aug;
+    float* aug_b0 = aug_warp + (size_t)n_warp * FF;
+    float* aug_b1 = aug_b0 + (size_t)pl.n_bucket[0] * FF;
+    float* aug_b2 = aug_b1 + (size_t)pl.n_bucket[1] * FF;
+    float* aug_split = aug_b2 + (size_t)pl.n_bucket[2] * FF;
     rc = launch_split<F, ENG>(h, pl, side, p, mode, aug_split, masks_out);
     if (rc) return rc;
     const int32_t* lists = pl.d_lists;
@@ -611,31 +615,21 @@ int run_side(als_handle* h, const Plan& pl, const Side& side, int mode, float* X
     rc = launch_cta_bucket<F, Caps<F>::c0, ENG>(h, side, p, lists + pl.off_bucket(0), pl.n_bucket[0], mode, aug_b0,
                                                masks_out);
     if (rc) return rc;
-    struct Seg { const int32_t* list; int count; float* aug; };
-    const Seg segs[4] = {{lists + pl.off_split(), pl.n_slots, aug_split},
-                         {lists + pl.off_bucket(0), pl.n_bucket[0], aug_b0},
-                         {lists + pl.off_bucket(1), pl.n_bucket[1], aug_b1},
-                         {lists + pl.off_bucket(2), pl.n_bucket[2], aug_b2}};
-    for (const Seg& sg : segs) {
-        if (sg.count == 0) continue;
-        if (mode == 0) {
-            rc = launch_solve<F>(h, sg.aug, sg.list, sg.count, p, X_out, flags_out, fb);
-            if (rc) return rc;
-        } else if (mode == 1) {
-            ALS_LAUNCH(h, "unpack_aug", als::k_unpack_aug<F><<<1024, 256, 0, st>>>(sg.aug, sg.list, sg.count, p.f,
-                                                                                    G_out, b_out));
-        }
-    }
     if constexpr (F <= 32) {
-        if (pl.n_warp > 0) {
-            ALS_LAUNCH(h, "warp_rows", als::k_warp_rows<F><<<(pl.n_warp + 7) / 8, 256, 0, st>>>(
-                                           side, p, lists, pl.n_warp, mode, X_out, flags_out, masks_out, G_aug,
-                                           counters(h), fb));
-            if (mode == 1)
-                ALS_LAUNCH(h, "unpack_aug", als::k_unpack_aug<F><<<1024, 256, 0, st>>>(G_aug, lists, pl.n_warp, p.f,
-                                                                                        G_out, b_out));
-        }
+        if (n_warp > 0)
+            ALS_LAUNCH(h, "warp_rows", als::k_warp_rows<F><<<(n_warp + 7) / 8, 256, 0, st>>>(
+                                           side, p, lists, n_warp, mode == 2, masks_out, aug_warp));
     }
+    if (mode == 0) {
+        rc = launch_solve<F>(h, G_aug, lists, n_aug, p, X_out, flags_out, fb);
+        if (rc) return rc;
+    } else if (mode == 1 && n_aug > 0) {
+        ALS_LAUNCH(h, "unpack_aug", als::k_unpack_aug<F><<<1024, 256, 0, st>>>(G_aug, lists, n_aug, p.f, G_out, b_out));
+    }
+    // The CTA and split rows (contiguous after the warp rows) are refined;
+    // warp rows always assemble in FP32 on CUDA cores.
+    struct Seg { const int32_t* list; int count; float* aug; };
+    const Seg segs[1] = {{lists + n_warp, pl.n_cta_like(), aug_b0}};
     if (refine) {
         // Refinement steps for the CTA and split rows: residual from the data
         // into the rhs column, another solve of the same G, X += delta.

@@ -1,17 +1,17 @@
 // Kernels of one Core-ALS half-sweep on CUDA cores (FP32), n_f <= 32.
 //
 // Rows are bucketed by length by the host planner:
-//   * k_warp_rows  : n_i <= 32. One warp per row does CES (Algorithm 1),
-//                    the Gram assembly of Eq. (core_ui) and the solve, all in
-//                    registers and a warp-private shared-memory tile.
+//   * k_warp_rows  : n_i <= 32. One warp per row does CES (Algorithm 1) and
+//                    the Gram assembly of Eq. (core_ui) in registers and a
+//                    warp-private shared-memory tile.
 //   * k_cta_rows   : 32 < n_i <= 1024 (three capacity buckets). One CTA per
 //                    row stages the slice in shared memory once, selects by
 //                    an exact radix select and assembles the masked Gram.
 //   * k_split_*    : n_i > 1024. The row is cut into 512-element chunks, one
 //                    CTA each; the radix passes meet in per-row global
 //                    histograms and the chunk Grams are summed in chunk order.
-//   The augmented systems [G | b] of the CTA and split rows are solved by
-//   k_solve_rows (warp per row).
+//   The augmented systems [G | b] of all rows are solved by one batched
+//   k_solve_rows launch (warp per system).
 #pragma once
 
 #include "als_device.cuh"
@@ -21,9 +21,9 @@ namespace als {
 constexpr int kWarpRowMax = 32;
 
 // ---------------------------------------------------------------------------
-// Warp per row (n_i <= 32).
-// mode 0: solve and write X; 1: write the augmented system to G_aug (indexed
-// by list position); 2: masks only.
+// Warp per row (n_i <= 32): gather, CES and the masked Gram of the row; the
+// augmented system [G | b] (regulariser added, padding rows identity) goes
+// to G_aug[w] for the batched solve. masks_only: stop after the masks.
 template <int F>
 struct WarpRowTile {
     union {
@@ -36,11 +36,9 @@ struct WarpRowTile {
 };
 
 template <int F>
-__global__ void __launch_bounds__(256) k_warp_rows(Side side, Params p, const int32_t* __restrict__ rows,
-                                                   int n_list, int mode, float* __restrict__ X_out,
-                                                   int32_t* __restrict__ flags_out,
-                                                   uint32_t* __restrict__ masks_out,
-                                                   float* __restrict__ G_aug, Counters* cnt, Fallback fb) {
+__global__ void __launch_bounds__(256, 4) k_warp_rows(Side side, Params p, const int32_t* __restrict__ rows,
+                                                   int n_list, bool masks_only, uint32_t* __restrict__ masks_out,
+                                                   float* __restrict__ G_aug) {
     __shared__ WarpRowTile<F> tiles[8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int w = blockIdx.x * 8 + warp;
@@ -77,7 +75,7 @@ __global__ void __launch_bounds__(256) k_warp_rows(Side side, Params p, const in
         for (int a = 0; a < f; ++a) word |= ((T.sel[a] >> lane) & 1u) << a;
         masks_out[lo + lane] = word;
     }
-    if (mode == 2) return;
+    if (masks_only) return;
 
     // Masked Gram: G[a][b] = sum_k w_ka x_ka w'_kb x_kb, b_a = sum_k w_ka x_ka r_k
     // with w the keep mask and w' = w (symmetric variant) or 1.
@@ -125,25 +123,8 @@ __global__ void __launch_bounds__(256) k_warp_rows(Side side, Params p, const in
         T.u.G[lane][lane] = (lane < f) ? T.u.G[lane][lane] + reg : 1.f;
     }
     __syncwarp();
-    if (mode == 1) {
-        float* dst = G_aug + (int64_t)w * F * (F + 1);
-        for (int e = lane; e < F * (F + 1); e += 32) dst[e] = T.u.G[e / (F + 1)][e % (F + 1)];
-        return;
-    }
-    float v[F];
-#pragma unroll
-    for (int j = 0; j < F; ++j) v[j] = (lane < F) ? T.u.G[lane][j] : 0.f;
-    const float rhs = (lane < F) ? T.u.G[lane][F] : 0.f;
-    float x;
-    int flags;
-    float ratio;
-    warp_solve<F>(v, rhs, f, p.gram_mode == GRAM_ASYM, p.ratio_max, x, flags, ratio);
-    if (lane < f) X_out[i * f + lane] = x;
-    if (lane == 0) {
-        if (flags_out) flags_out[i] = flags;
-        record_flags(cnt, flags, ratio);
-        fallback_push(fb, flags, i);
-    }
+    float* dst = G_aug + (int64_t)w * F * (F + 1);
+    for (int e = lane; e < F * (F + 1); e += 32) dst[e] = T.u.G[e / (F + 1)][e % (F + 1)];
 }
 
 }  // namespace als

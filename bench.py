@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--precision", choices=["fp32", "tf32", "bf16", "fp32_tc"], default="fp32")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--workload", choices=["zipf_100k", "zipf_1m"], default="zipf_100k",
+                    help="zipf_1m: the 1M x 100k, 10^8-cell matrix drawn on the device, fitted at --nf")
+    ap.add_argument("--nf", type=int, default=64, help="model width for --workload zipf_1m (64 or 128)")
     return ap.parse_args()
 
 
@@ -375,8 +378,94 @@ def time_to_rmse(p, w, M0, settings, sweeps=15):
     return res
 
 
+def large_arm(args):
+    """--workload zipf_1m: sweep throughput at n_f = 64 / 128 on the
+    10^8-cell matrix (drawn on the device), the error of one user half-sweep
+    against the FP64 oracle on 10,000 sampled rows, and the oracle's own rate
+    on that sample."""
+    import torch
+    import oracle
+    from paper_2509_18024_gb300 import core_als
+    w = dict(synth.WORKLOADS["zipf_1m"])
+    f, lam = args.nf, w["lam"]
+    r = args.budget if args.budget is not None else w["budget"]
+    t0 = time.perf_counter()
+    d = synth.zipf_ratings_device(w["n_u"], w["n_m"], w["f"], w["nnz"], w["zipf_s"], w["noise_sd"], args.seed)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    Ru = core_als.DeviceCSR(w["n_u"], w["n_m"], *d.rows)
+    Ri = core_als.DeviceCSR(w["n_m"], w["n_u"], *d.cols)
+    M0 = synth.init_factor(w["n_m"], f, 1000)
+    eng = core_als.CoreALS(f, lam, r, precision=PRECISIONS[args.precision])
+    M = torch.as_tensor(M0).cuda()
+    U = torch.empty((w["n_u"], f), dtype=torch.float32, device="cuda")
+    # Error of one half-sweep from M^(0) against the FP64 oracle on a sample.
+    eng.half_sweep(Ru, M, U)
+    rng = np.random.default_rng(args.seed)
+    rows = np.sort(rng.choice(w["n_u"], size=10000, replace=False))
+    indptr, indices, values = (t.cpu().numpy() for t in d.rows)
+    t1 = time.perf_counter()
+    Xo, _, _ = oracle.half_sweep(indptr, indices, values, M0.astype(np.float64), lam, r, oracle.GRAM_ASYM,
+                                 rows=rows)
+    t_or = time.perf_counter() - t1
+    Xg = U.cpu().numpy()[rows].astype(np.float64)
+    Xo = Xo[rows]
+    err = float(np.linalg.norm(Xg - Xo) / np.linalg.norm(Xo))
+    row_err = np.linalg.norm(Xg - Xo, axis=1) / np.maximum(np.linalg.norm(Xo, axis=1), 1e-300)
+    L = np.diff(indptr)
+    or_rate = w["n_u"] * 1.0 / (t_or * Ru.nnz / max(int(L[rows].sum()), 1))  # user rows/s, by entries
+    # Throughput.
+    sse = torch.zeros(1, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step():
+        eng.half_sweep(Ru, M, U)
+        eng.half_sweep(Ri, U, M)
+        eng.sse_async(d.test_u, d.test_m, d.test_r, U, M, sse)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = eng.launch_count
+    eng.profile(True)
+    with ClockSampler(0) as clk:
+        for q in range(args.steps):
+            flush.zero_()
+            evs[q][0].record(stream)
+            step()
+            evs[q][1].record(stream)
+        torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    fam = {k: eng.kernel_time(k) for k in KERNEL_FAMILIES + ("refine_resid", "fp64_rows", "add_rows")}
+    fam = {k: v for k, v in fam.items() if v[1]}
+    eng.profile(False)
+    n_rows = w["n_u"] + w["n_m"]
+    out = {"metric": METRIC, "value": n_rows * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic (device-drawn Zipf)",
+           "config": {"workload": f"zipf_1m: {w['n_u']} users x {w['n_m']} items, {w['nnz']} cells (Zipf "
+                                  f"{w['zipf_s']}), n_f={f}, lambda={lam}, r={r}, asymmetric Eq. core_ui",
+                      "n_f": f, "precision": args.precision, "refine_steps": "auto",
+                      "l2": "flushed between steps (256 MB write)", "generation_s": round(gen_s, 1)},
+           "gpu_launches": eng.launch_count - launches0, "clocks": clk.summary(),
+           "kernels_ms_per_step": {k: v[0] / args.steps for k, v in fam.items()},
+           "error_vs_fp64_oracle": {"sample_rows": len(rows), "rel_fro": err, "row_rel_max": float(row_err.max()),
+                                    "row_rel_p99": float(np.quantile(row_err, 0.99)),
+                                    "what": "one user half-sweep from the same M^(0)"},
+           "cpu_baseline": {"value": or_rate, "unit": "user row-solves/s", "cores": oracle.num_threads(),
+                            "kind": "oracle", "sample": f"{len(rows)} random user rows, one half-sweep, "
+                                                       f"extrapolated by observed entries"},
+           "test_rmse_after_timed_sweeps": float(np.sqrt(sse.item() / d.test_r.numel()))}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "zipf_1m":
+        large_arm(args)
+        return 0
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -203,6 +203,10 @@ WORKLOADS = {
                   noise_sd=0.1, lam=0.1, budget=0.5, sweeps=10),
     "zipf_100k": dict(kind="zipf", n_u=100_000, n_m=20_000, f=32, nnz=10_000_000,
                       zipf_s=1.0, noise_sd=0.5, lam=0.05, budget=0.25, sweeps=15),
+    # 1M x 100k, 10^8 cells, Zipf(0.8), rank-32 truth; drawn on the device
+    # (zipf_ratings_device), fitted at n_f = 64 or 128.
+    "zipf_1m": dict(kind="zipf_device", n_u=1_000_000, n_m=100_000, f=32, nnz=100_000_000,
+                    zipf_s=0.8, noise_sd=0.5, lam=0.05, budget=0.25, sweeps=15),
 }
 
 
@@ -211,4 +215,78 @@ def make_workload(name: str, seed: int = 1, **over) -> RatingProblem:
     w.update(over)
     if w["kind"] == "uniform":
         return uniform_lowrank(w["n_u"], w["n_m"], w["f"], w["density"], w["noise_sd"], seed)
+    if w["kind"] == "zipf_device":
+        raise ValueError(f"{name} is drawn on the device: use zipf_ratings_device")
     return zipf_ratings(w["n_u"], w["n_m"], w["f"], w["nnz"], w["zipf_s"], w["noise_sd"], seed)
+
+
+# ---------------------------------------------------------------------------
+# Device-side generator for the workloads too large to draw on the host in
+# reasonable time (10^8 cells). Same recipe as zipf_ratings: Zipf(s) user and
+# item popularity with randomly permuted ranks, distinct cells drawn from the
+# product law, integer 1-5 ratings clip(rint(3 + u.v + eps), 1, 5) from a
+# rank-`f` truth with N(0, 1/sqrt(f)) (variance) entries, 90/10 train/test.
+# Seeded through torch's counter-based CUDA generator, so a (seed, sizes,
+# torch build) triple gives the same matrix; it is not the host generator's
+# stream, so its matrices differ from zipf_ratings' for the same seed.
+@dataclass
+class DeviceRatingProblem:
+    n_u: int
+    n_m: int
+    f: int
+    rows: tuple   # (indptr int64, indices int32, values float32) of train, users x items
+    cols: tuple   # the same for items x users
+    test_u: "object"
+    test_m: "object"
+    test_r: "object"
+
+
+def zipf_ratings_device(n_u: int, n_m: int, f: int, nnz: int, zipf_s: float, noise_sd: float, seed: int,
+                        device="cuda") -> DeviceRatingProblem:
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    std = (1.0 / np.sqrt(f)) ** 0.5
+    U = torch.randn((n_u, f), generator=g, device=device) * std
+    M = torch.randn((n_m, f), generator=g, device=device) * std
+
+    def cdf(n):
+        w = 1.0 / torch.arange(1, n + 1, dtype=torch.float64, device=device) ** zipf_s
+        w = w[torch.randperm(n, generator=g, device=device)]
+        return torch.cumsum(w / w.sum(), 0)
+
+    cu, cm = cdf(n_u), cdf(n_m)
+    have = torch.empty(0, dtype=torch.int64, device=device)
+    while have.numel() < nnz:
+        want = int((nnz - have.numel()) * 1.3) + 1024
+        i = torch.clamp(torch.searchsorted(cu, torch.rand(want, generator=g, device=device, dtype=torch.float64)),
+                        max=n_u - 1)
+        j = torch.clamp(torch.searchsorted(cm, torch.rand(want, generator=g, device=device, dtype=torch.float64)),
+                        max=n_m - 1)
+        have = torch.unique(torch.cat([have, i * n_m + j]))
+    keep = torch.randperm(have.numel(), generator=g, device=device)[:nnz]
+    cells = have[torch.sort(keep).values]
+    del have, keep
+    ii, jj = cells // n_m, cells % n_m
+    rr = torch.empty(nnz, dtype=torch.float32, device=device)
+    step = 1 << 23
+    for s in range(0, nnz, step):
+        a, b = ii[s:s + step], jj[s:s + step]
+        rr[s:s + step] = (U[a] * M[b]).sum(1)
+    rr = torch.clamp(torch.round(3.0 + rr + torch.randn(nnz, generator=g, device=device) * noise_sd), 1.0, 5.0)
+    is_test = torch.zeros(nnz, dtype=torch.bool, device=device)
+    is_test[torch.randperm(nnz, generator=g, device=device)[:int(round(nnz * 0.1))]] = True
+    tr = ~is_test
+
+    def csr(r_idx, c_idx, vals, n_rows, n_cols):
+        key = r_idx * n_cols + c_idx
+        order = torch.argsort(key)
+        counts = torch.bincount(r_idx, minlength=n_rows)
+        indptr = torch.zeros(n_rows + 1, dtype=torch.int64, device=device)
+        indptr[1:] = torch.cumsum(counts, 0)
+        return indptr, c_idx[order].to(torch.int32).contiguous(), vals[order].contiguous()
+
+    rows = csr(ii[tr], jj[tr], rr[tr], n_u, n_m)
+    cols = csr(jj[tr], ii[tr], rr[tr], n_m, n_u)
+    return DeviceRatingProblem(n_u, n_m, f, rows, cols, ii[is_test].to(torch.int32), jj[is_test].to(torch.int32),
+                               rr[is_test])

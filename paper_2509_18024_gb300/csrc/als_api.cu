@@ -104,6 +104,7 @@ struct als_handle {
     DevBuf masks;     // CES masks of the current half-sweep (FP64 fallback)
     DevBuf fb_list;   // rows flagged for the FP64 redo
     DevBuf delta;     // refinement corrections
+    DevBuf perms;     // pivot permutations of the stored LU factors (n_f > 32, refinement)
     int n_sm = 152;
     int64_t launches = 0;
     std::string last_error;
@@ -475,13 +476,9 @@ int launch_cta_bucket(als_handle* h, const Side& side, const Params& p, const in
     return ALS_OK;
 }
 
-template <int F, int ENG>
-int launch_split(als_handle* h, const Plan& pl, const Side& side, const Params& p, int mode, float* G_aug,
-                 uint32_t* masks_out) {
-    if (pl.n_slots == 0) return ALS_OK;
-    cudaStream_t st = h->stream;
+// Device views of a plan's split rows (chunk lists) and their state.
+void split_views(const Plan& pl, int F, als::SplitPlan& sp, als::SplitState& ss) {
     const int32_t* base = pl.d_lists;
-    als::SplitPlan sp;
     sp.row = base + pl.off_split();
     sp.c_begin = sp.row + pl.n_slots;
     sp.ch_slot = sp.c_begin + pl.n_slots + 1;
@@ -493,7 +490,6 @@ int launch_split(als_handle* h, const Plan& pl, const Side& side, const Params& 
     sp.n_super = pl.n_super;
     const SplitLayout L(pl.n_slots, pl.n_chunks, F);
     char* mem = reinterpret_cast<char*>(pl.d_split);
-    als::SplitState ss;
     ss.P = reinterpret_cast<uint32_t*>(mem + L.P);
     ss.Mk = reinterpret_cast<uint32_t*>(mem + L.Mk);
     ss.need = reinterpret_cast<int32_t*>(mem + L.need);
@@ -503,6 +499,16 @@ int launch_split(als_handle* h, const Plan& pl, const Side& side, const Params& 
     ss.arrive = reinterpret_cast<int32_t*>(mem + L.arrive);
     ss.eqc = reinterpret_cast<int32_t*>(mem + L.eqc);
     ss.part = reinterpret_cast<float*>(mem + L.part);
+}
+
+template <int F, int ENG>
+int launch_split(als_handle* h, const Plan& pl, const Side& side, const Params& p, int mode, float* G_aug,
+                 uint32_t* masks_out) {
+    if (pl.n_slots == 0) return ALS_OK;
+    cudaStream_t st = h->stream;
+    als::SplitPlan sp;
+    als::SplitState ss;
+    split_views(pl, F, sp, ss);
     const int sc = pl.n_slots * F;
     ALS_LAUNCH(h, "split_init", als::k_split_init<F><<<(sc + 255) / 256, 256, 0, st>>>(side, p, sp, ss));
     const size_t hsmem = (size_t)F * als::kHistRow * 4;
@@ -531,18 +537,20 @@ int launch_split(als_handle* h, const Plan& pl, const Side& side, const Params& 
 
 // Batched solve of augmented systems listed by `list` (null: identity).
 template <int F>
-int launch_solve(als_handle* h, const float* aug, const int32_t* list, int count, const Params& p, float* X_out,
-                 int32_t* flags_out, als::Fallback fb, Counters* cnt = nullptr) {
+int launch_solve(als_handle* h, float* aug, const int32_t* list, int count, const Params& p, float* X_out,
+                 int32_t* flags_out, als::Fallback fb, Counters* cnt = nullptr, int32_t* perm_buf = nullptr,
+                 int replay = 0) {
     if (count == 0) return ALS_OK;
     if (cnt == nullptr) cnt = counters(h);
     if constexpr (F <= 32) {
         ALS_LAUNCH(h, "solve_rows", als::k_solve_rows<F><<<(count + 7) / 8, 256, 0, h->stream>>>(
                                         aug, list, count, p, X_out, flags_out, cnt, fb));
     } else {
-        const size_t smem = (size_t)F * (F + 1) * sizeof(float);
-        ALS_CUDA(h, cudaFuncSetAttribute(als::k_solve_big<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        ALS_LAUNCH(h, "solve_rows", als::k_solve_big<F><<<count, als::kBigSolveThreads, smem, h->stream>>>(
-                                        aug, list, count, p, X_out, flags_out, cnt, fb));
+        using C = als::BigSolve<F>;
+        ALS_CUDA(h, cudaFuncSetAttribute(als::k_solve_big<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
+        ALS_LAUNCH(h, "solve_rows", als::k_solve_big<F><<<count, C::NT, C::SMEM, h->stream>>>(
+                                        aug, list, count, p, X_out, flags_out, cnt, fb, perm_buf,
+                                        perm_buf != nullptr && !replay, replay));
     }
     return ALS_OK;
 }
@@ -620,8 +628,16 @@ int run_side(als_handle* h, const Plan& pl, const Side& side, int mode, float* X
             ALS_LAUNCH(h, "warp_rows", als::k_warp_rows<F><<<(n_warp + 7) / 8, 256, 0, st>>>(
                                            side, p, lists, n_warp, mode == 2, masks_out, aug_warp));
     }
+    // Wide systems keep their LU factors (in G_aug) and permutations when a
+    // refinement follows: its corrections then need substitutions only.
+    int32_t* perm_buf = nullptr;
+    if (F > 32 && refine) {
+        rc = ensure(h, h->perms, (size_t)std::max(n_aug, 1) * F * sizeof(int32_t));
+        if (rc) return rc;
+        perm_buf = reinterpret_cast<int32_t*>(h->perms.p);
+    }
     if (mode == 0) {
-        rc = launch_solve<F>(h, G_aug, lists, n_aug, p, X_out, flags_out, fb);
+        rc = launch_solve<F>(h, G_aug, lists, n_aug, p, X_out, flags_out, fb, nullptr, perm_buf);
         if (rc) return rc;
     } else if (mode == 1 && n_aug > 0) {
         ALS_LAUNCH(h, "unpack_aug", als::k_unpack_aug<F><<<1024, 256, 0, st>>>(G_aug, lists, n_aug, p.f, G_out, b_out));
@@ -632,17 +648,34 @@ int run_side(als_handle* h, const Plan& pl, const Side& side, int mode, float* X
     const Seg segs[1] = {{lists + n_warp, pl.n_cta_like(), aug_b0}};
     if (refine) {
         // Refinement steps for the CTA and split rows: residual from the data
-        // into the rhs column, another solve of the same G, X += delta.
+        // into the rhs column, a solve with the same G (for n_f > 32 the
+        // stored factors: substitutions only), X += delta.
         rc = ensure(h, h->delta, (size_t)std::max<int64_t>(pl.n_rows, 1) * p.f * sizeof(float));
         if (rc) return rc;
         float* D = reinterpret_cast<float*>(h->delta.p);
         for (int step = 0; step < h->opt.refine_steps; ++step)
         for (const Seg& sg : segs) {
             if (sg.count == 0) continue;
-            ALS_LAUNCH(h, "refine_resid", als::k_refine_resid<F><<<sg.count, als::kRefineThreads, 0, st>>>(
-                                              side, p, masks_out, sg.list, sg.count, sg.aug, X_out));
+            // Resident-bucket rows: a warp each; split rows: a CTA each.
+            const int nb = pl.n_bucket[0] + pl.n_bucket[1] + pl.n_bucket[2];
+            if (nb > 0)
+                ALS_LAUNCH(h, "refine_resid", als::k_refine_resid_warp<F><<<(nb + 7) / 8, 256, 0, st>>>(
+                                                  side, p, masks_out, sg.list, nb, sg.aug, X_out));
+            if (pl.n_slots > 0) {
+                // Chunk partials (FP64) in the split state's chunk-Gram scratch,
+                // free once the systems are assembled; then a fixed-order sum.
+                als::SplitPlan sp;
+                als::SplitState ss;
+                split_views(pl, F, sp, ss);
+                double* part = reinterpret_cast<double*>(ss.part);
+                ALS_LAUNCH(h, "refine_resid", als::k_refine_resid_chunk<F><<<pl.n_chunks, 256, 0, st>>>(
+                                                  side, p, sp, masks_out, part, X_out));
+                ALS_LAUNCH(h, "refine_resid", als::k_refine_resid_reduce<F><<<pl.n_slots, 128, 0, st>>>(
+                                                  side, p, sp, part, sg.aug + (size_t)nb * F * (F + 1), X_out));
+            }
             rc = launch_solve<F>(h, sg.aug, sg.list, sg.count, p, D, nullptr, als::Fallback{nullptr, nullptr},
-                                 scratch_counters(h));
+                                 scratch_counters(h), perm_buf ? perm_buf + (size_t)n_warp * F : nullptr,
+                                 perm_buf != nullptr);
             if (rc) return rc;
             ALS_LAUNCH(h, "add_rows", als::k_add_rows<<<std::min(1024, (sg.count * p.f + 255) / 256), 256, 0, st>>>(
                                           sg.list, sg.count, p.f, D, X_out));
@@ -776,7 +809,7 @@ int als_destroy(als_handle* h) {
     }
     for (auto e : h->event_pool) cudaEventDestroy(e);
     if (h->fit_graph.exec) cudaGraphExecDestroy(h->fit_graph.exec);
-    for (DevBuf* b : {&h->g_aug, &h->misc, &h->host_in, &h->masks, &h->fb_list, &h->delta})
+    for (DevBuf* b : {&h->g_aug, &h->misc, &h->host_in, &h->masks, &h->fb_list, &h->delta, &h->perms})
         if (b->p) cudaFree(b->p);
     delete h;
     return ALS_OK;

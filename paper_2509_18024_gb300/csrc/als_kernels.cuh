@@ -429,6 +429,186 @@ __global__ void __launch_bounds__(BigSolve<F>::NT) k_solve_big(float* __restrict
     }
 }
 
+// Register-resident LU for widths above 32: one thread per matrix row, the row
+// (F + 1 values with the rhs) in registers. Columns are eliminated in blocks
+// of 8 steps; between blocks every row shifts its registers left by 8, so
+// that the pivot column of step s of a block is always register s (all
+// register indices are compile-time). Step k: every live row offers |a_ik|
+// (warp max + lowest row), the pivot is the largest over the CTA (lowest row
+// on ties; row k itself for the symmetric modes), its row is published as
+// float4s into U[k] (shared memory, U in step order), and every live row
+// subtracts l_ik U[k] with l_ik = a_ik / u_kk, keeping l_ik in the dead
+// register. One warp back-substitutes from U. Same pivots, products and
+// rounding as k_solve_big. store != 0: each row's block of L / U entries goes
+// back to G_aug (L before the row's own pivot step, U from it on) and the
+// physical row of each step to perm_buf, as k_solve_big stores them.
+template <int F>
+struct RegSolve {
+    static constexpr int NT = F;      // threads per system
+    static constexpr int NW = F / 32;
+    static constexpr int R = F + 1;   // registers per row (with the rhs)
+    static constexpr int P = F + 4;   // U row pitch (floats)
+    static constexpr int NCH = (R + 3) / 4;
+    static constexpr size_t SMEM = (size_t)F * P * sizeof(float);
+};
+
+template <int F>
+__global__ void __launch_bounds__(RegSolve<F>::NT, F == 64 ? 8 : 2) k_solve_reg(
+    float* __restrict__ G_aug, const int32_t* __restrict__ rows, int n_list, Params p, float* __restrict__ X_out,
+    int32_t* __restrict__ flags_out, Counters* cnt, Fallback fb, int32_t* __restrict__ perm_buf, int store) {
+    using C = RegSolve<F>;
+    constexpr int NW = C::NW, R = C::R, P = C::P;
+    extern __shared__ __align__(16) float smem_f[];
+    float (*U)[P] = reinterpret_cast<float (*)[P]>(smem_f);
+    __shared__ uint32_t s_key[2][NW];
+    __shared__ int s_idx[2][NW];
+    __shared__ float s_dinv[F];
+    __shared__ float s_pv[F];
+    __shared__ int s_ord[F];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int w = blockIdx.x;
+    if (w >= n_list) return;
+    float* src = G_aug + (int64_t)w * F * (F + 1);
+    // Stage coalesced through U, then each thread takes its row.
+    for (int e = tid; e < F * (F + 1); e += F) U[e / (F + 1)][e % (F + 1)] = src[e];
+    __syncthreads();
+    float r[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) r[j] = U[tid][j];
+    __syncthreads();
+    const bool pivot = p.gram_mode == GRAM_ASYM;
+    bool live = true;
+    for (int t = 0; t < F / 8; ++t) {
+        const int rem = R - 8 * t;  // registers still holding columns 8t .. F
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const int k = 8 * t + s;
+            uint32_t key;
+            if (pivot) key = live ? __float_as_uint(fabsf(r[s])) + 1u : 0u;
+            else key = tid == k ? 1u : 0u;
+            const uint32_t m = __reduce_max_sync(kFull, key);
+            const unsigned bal = __ballot_sync(kFull, key == m && m != 0u);
+            if (lane == 0) {
+                s_key[k & 1][warp] = m;
+                s_idx[k & 1][warp] = bal ? warp * 32 + __ffs(bal) - 1 : F;
+            }
+            __syncthreads();
+            uint32_t bm = 0u;
+            int pidx = F;
+#pragma unroll
+            for (int v = 0; v < NW; ++v) {
+                const uint32_t kv = s_key[k & 1][v];
+                const int iv = s_idx[k & 1][v];
+                if (kv > bm || (kv == bm && iv < pidx)) {
+                    bm = kv;
+                    pidx = iv;
+                }
+            }
+            if (tid == pidx) {
+                float* urow = &U[k][8 * t];
+#pragma unroll
+                for (int c = 0; c < C::NCH; ++c) {
+                    if (4 * c < rem) {
+                        if (4 * c + 3 < R) {
+                            *reinterpret_cast<float4*>(urow + 4 * c) = make_float4(r[4 * c], r[4 * c + 1], r[4 * c + 2], r[4 * c + 3]);
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                if (4 * c + e < R) urow[4 * c + e] = r[4 * c + e];
+                        }
+                    }
+                }
+                const float pv = r[s];
+                s_pv[k] = pv;
+                s_dinv[k] = pv != 0.f ? 1.0f / pv : 0.f;
+                s_ord[k] = tid;
+                live = false;
+            }
+            __syncthreads();
+            const float di = s_dinv[k];
+            if (live && di != 0.f) {
+                const float l = r[s] * di;
+                r[s] = l;
+                const float* urow = &U[k][8 * t];
+#pragma unroll
+                for (int c = (s + 1) / 4; c < C::NCH; ++c) {
+                    if (4 * c < rem) {
+                        float u4[4];
+                        if (4 * c + 3 < R) {
+                            const float4 v = *reinterpret_cast<const float4*>(urow + 4 * c);
+                            u4[0] = v.x;
+                            u4[1] = v.y;
+                            u4[2] = v.z;
+                            u4[3] = v.w;
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) u4[e] = (4 * c + e < R) ? urow[4 * c + e] : 0.f;
+                        }
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int j = 4 * c + e;
+                            if (j > s && j < R) r[j] = fmaf(-l, u4[e], r[j]);
+                        }
+                    }
+                }
+            }
+        }
+        if (store) {
+            float* dst = src + (int64_t)tid * (F + 1) + 8 * t;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) dst[e] = r[e];
+        }
+#pragma unroll
+        for (int j = 0; j + 8 < R; ++j) r[j] = r[j + 8];
+    }
+    __syncthreads();
+    bool singular = false;
+    float pmax = 0.f, pmin = __int_as_float(0x7f800000);
+    if (tid == 0)
+        for (int k = 0; k < p.f; ++k) {
+            const float apv = pivot ? fabsf(s_pv[k]) : s_pv[k];
+            if (!(apv > 0.f)) singular = true;
+            pmax = fmaxf(pmax, apv);
+            pmin = fminf(pmin, apv);
+        }
+    // Back substitution by warp 0 on U (rows in step order): lane holds
+    // steps lane + 32 s2.
+    if (warp == 0) {
+        constexpr int S = F / 32;
+        float y[S];
+#pragma unroll
+        for (int s2 = 0; s2 < S; ++s2) y[s2] = U[lane + 32 * s2][F];
+        const int64_t i = rows ? (int64_t)rows[w] : (int64_t)w;
+        float* xo = X_out + i * p.f;
+        const bool sing = __shfl_sync(kFull, (int)singular, 0) != 0;
+#pragma unroll
+        for (int k = F - 1; k >= 0; --k) {
+            const float yk = __shfl_sync(kFull, y[k / 32], k % 32);
+            const float xk = yk * s_dinv[k];
+            if (lane == k % 32 && k < p.f) xo[k] = sing ? 0.f : xk;
+#pragma unroll
+            for (int s2 = 0; s2 < S; ++s2)
+                if (lane + 32 * s2 < k) y[s2] = fmaf(-U[lane + 32 * s2][k], xk, y[s2]);
+        }
+    }
+    if (store)
+        for (int k = tid; k < F; k += F) perm_buf[(int64_t)w * F + k] = s_ord[k];
+    if (tid == 0) {
+        int flags = 0;
+        float ratio = (p.f > 0) ? pmax / pmin : 1.f;
+        if (singular) {
+            flags = FLAG_SINGULAR | FLAG_RATIO;
+            ratio = __int_as_float(0x7f800000);
+        } else if (!(ratio <= p.ratio_max)) {
+            flags = FLAG_RATIO;
+        }
+        const int64_t i = rows ? (int64_t)rows[w] : (int64_t)w;
+        if (flags_out) flags_out[i] = flags;
+        record_flags(cnt, flags, ratio);
+        fallback_push(fb, flags, i);
+    }
+}
+
 // Pack f x f systems (plus rhs) from user buffers into the padded augmented layout.
 template <int F>
 __global__ void k_pack_aug(const float* __restrict__ G, const float* __restrict__ b, int64_t n_rows, int f,

@@ -250,6 +250,28 @@ KERNEL_FAMILIES = ("cta_rows", "warp_rows", "solve_rows", "split_init", "split_h
                    "split_cut", "split_gram", "split_reduce", "sse", "sum_partials")
 
 
+# DRAM traffic of the dominant kernel family, from the one-pass ncu capture
+# summarised in profiles/cta_rows_zipf100k_traffic.md (dram__bytes_read.sum +
+# dram__bytes_write.sum, averaged over the 6 k_cta_rows launches of a sweep).
+# It holds only for the kernel sources it was taken from: `roofline.traffic`
+# is null once their hash differs.
+TRAFFIC = {"kernel": "cta_rows", "bytes_per_launch": 44.70e6, "sources_sha256_16": "96009b0c79c67620"}
+
+
+def kernel_sources_hash():
+    import glob
+    import hashlib
+    pkg = os.path.join(ROOT, "paper_2509_18024_gb300", "csrc")
+    files = sorted(glob.glob(os.path.join(pkg, "*.cu")) + glob.glob(os.path.join(pkg, "*.cuh")))
+    files.append(os.path.join(ROOT, "include", "core_als.h"))
+    h = hashlib.sha256()
+    for fn in files:
+        h.update(os.path.basename(fn).encode())
+        with open(fn, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def roofline(top, avg_s, p, f, r):
     """Roofline entry of the dominant kernel family: algorithmic FP32 flops
     of the rows it handles (2 s_i f^2 for X*^T X plus 2 s_i f for X*^T r, with
@@ -273,8 +295,12 @@ def roofline(top, avg_s, p, f, r):
             flops += float((2 * s * f * f + 2 * s * f).sum())
     per_launch = flops / launches_per_sweep
     achieved = per_launch / avg_s / 1e12
+    traffic = None
+    if top == TRAFFIC["kernel"] and kernel_sources_hash() == TRAFFIC["sources_sha256_16"]:
+        traffic = TRAFFIC["bytes_per_launch"]
     return {"bound": "alu", "achieved": achieved, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP32_ALU_PEAK_TFLOPS, "traffic": None, "kernel": top,
+            "frac": achieved / FP32_ALU_PEAK_TFLOPS, "traffic": traffic, "traffic_unit": "bytes per launch",
+            "algorithmic_flops_per_launch": per_launch, "kernel": top,
             "avg_launch_ms": avg_s * 1e3,
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"}
 

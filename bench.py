@@ -55,7 +55,10 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--workload", choices=["zipf_100k", "zipf_1m"], default="zipf_100k",
                     help="zipf_1m: the 1M x 100k, 10^8-cell matrix drawn on the device, fitted at --nf")
-    ap.add_argument("--nf", type=int, default=64, help="model width for --workload zipf_1m (64 or 128)")
+    ap.add_argument("--nf", type=int, default=None,
+                    help="model width for --workload zipf_1m (default 64) or --capture-case (default 32)")
+    ap.add_argument("--capture-case", choices=sorted(synth.CAPTURE_CASES), default=None,
+                    help="run one half-sweep of a small single-bucket case three times (for ncu captures)")
     return ap.parse_args()
 
 
@@ -413,7 +416,7 @@ def large_arm(args):
     import oracle
     from paper_2509_18024_gb300 import core_als
     w = dict(synth.WORKLOADS["zipf_1m"])
-    f, lam = args.nf, w["lam"]
+    f, lam = args.nf or 64, w["lam"]
     r = args.budget if args.budget is not None else w["budget"]
     t0 = time.perf_counter()
     d = synth.zipf_ratings_device(w["n_u"], w["n_m"], w["f"], w["nnz"], w["zipf_s"], w["noise_sd"], args.seed)
@@ -487,8 +490,30 @@ def large_arm(args):
     print(json.dumps(out), flush=True)
 
 
+def capture_arm(args):
+    """Three half-sweeps of a small single-bucket case (a kernel capture
+    takes the second launch with -s 1 -c 1)."""
+    import torch
+    from paper_2509_18024_gb300 import core_als
+    f = args.nf or 32
+    r = args.budget if args.budget is not None else 0.25
+    csr, Y = synth.capture_case(args.capture_case, f)
+    eng = core_als.CoreALS(f, 0.05, r, precision=PRECISIONS[args.precision])
+    R = core_als.DeviceCSR.from_host(csr)
+    Yd = torch.as_tensor(Y).cuda()
+    X = torch.empty((csr.n_rows, f), device="cuda")
+    for _ in range(3):
+        eng.half_sweep(R, Yd, X)
+    torch.cuda.synchronize()
+    print(json.dumps({"capture_case": args.capture_case, "n_f": f, "budget": r, "precision": args.precision,
+                      "rows": csr.n_rows, "nnz": csr.nnz}), flush=True)
+
+
 def main():
     args = parse()
+    if args.capture_case:
+        capture_arm(args)
+        return 0
     if args.workload == "zipf_1m":
         large_arm(args)
         return 0

@@ -290,3 +290,28 @@ def zipf_ratings_device(n_u: int, n_m: int, f: int, nnz: int, zipf_s: float, noi
     cols = csr(jj[tr], ii[tr], rr[tr], n_m, n_u)
     return DeviceRatingProblem(n_u, n_m, f, rows, cols, ii[is_test].to(torch.int32), jj[is_test].to(torch.int32),
                                rr[is_test])
+
+
+# ---------------------------------------------------------------------------
+# Small single-side cases for kernel captures: rows of one length band with
+# distinct sorted column ids, N(0, 1) ratings and Y ~ N(0, 0.6^2) (30,000
+# columns). They isolate one row bucket of the half-sweep.
+CAPTURE_CASES = {
+    "rows1_32": (60_000, 1, 32),
+    "rows33_128": (20_000, 33, 128),
+    "rows129_512": (6_000, 129, 512),
+    "rows513_1024": (3_000, 513, 1024),
+    "split": (300, 2_000, 20_000),
+}
+
+
+def capture_case(name: str, f: int, seed: int = 0, n_cols: int = 30_000):
+    n_rows, lo, hi = CAPTURE_CASES[name]
+    rng = np.random.default_rng(seed)
+    lengths = rng.integers(lo, hi + 1, n_rows)
+    indptr = np.zeros(n_rows + 1, np.int64)
+    np.cumsum(lengths, out=indptr[1:])
+    idx = np.concatenate([np.sort(rng.choice(n_cols, size=int(L), replace=False)) for L in lengths])
+    vals = rng.standard_normal(int(lengths.sum())).astype(np.float32)
+    Y = (rng.standard_normal((n_cols, f)) * 0.6).astype(np.float32)
+    return CSR(n_rows, n_cols, indptr, idx.astype(np.int32), vals), Y

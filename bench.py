@@ -53,8 +53,9 @@ def parse():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--precision", choices=["fp32", "tf32", "bf16", "fp32_tc"], default="fp32")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--workload", choices=["zipf_100k", "zipf_1m"], default="zipf_100k",
-                    help="zipf_1m: the 1M x 100k, 10^8-cell matrix drawn on the device, fitted at --nf")
+    ap.add_argument("--workload", choices=["zipf_100k", "zipf_1m", "warmstart"], default="zipf_100k",
+                    help="zipf_1m: the 1M x 100k, 10^8-cell matrix drawn on the device, fitted at --nf; "
+                         "warmstart: the learned warm start on 100k x 20k matrices (5 training, 5 held-out seeds)")
     ap.add_argument("--nf", type=int, default=None,
                     help="model width for --workload zipf_1m (default 64) or --capture-case (default 32)")
     ap.add_argument("--capture-case", choices=sorted(synth.CAPTURE_CASES), default=None,
@@ -490,6 +491,55 @@ def large_arm(args):
     print(json.dumps(out), flush=True)
 
 
+def warmstart_arm(args):
+    """The learned warm start on the 100k x 20k shape: user and item nets
+    trained on the converged factors of 5 seeded matrices, judged on 5
+    held-out seeds against plain FP32 ALS from the same M^(0). For each
+    held-out matrix: sweeps and CUDA-event ms to the plain run's final test
+    RMSE x (1 + 1e-3), for warm starts fitted in FP32, TF32 and BF16 (the
+    warm runs' times include computing the warm start)."""
+    import torch
+    from paper_2509_18024_gb300 import warmstart
+    w = dict(synth.WORKLOADS["zipf_100k"])
+    f, lam = w["f"], w["lam"]
+    r = args.budget if args.budget is not None else w["budget"]
+    sweeps = w["sweeps"]
+
+    def draw(seed):
+        return synth.zipf_ratings_device(w["n_u"], w["n_m"], w["f"], w["nnz"], w["zipf_s"], w["noise_sd"], seed)
+
+    t0 = time.perf_counter()
+    nets, hist = warmstart.train([draw(s) for s in (101, 102, 103, 104, 105)], f, lam, r, sweeps=sweeps,
+                                 hidden=256, epochs=20, batch=4096)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    per_seed = []
+    for s in (201, 202, 203, 204, 205):
+        prob = draw(s)
+        M0 = synth.init_factor(w["n_m"], f, 5000 + s)
+        res = warmstart.judge(nets, prob, f, lam, r, M0, sweeps, precisions=(0, 1, 2))
+        per_seed.append({"seed": s, "target_rmse": res["target"], "chosen": res["chosen"],
+                         "warm_start_ms": res["warm_start_ms"],
+                         "sweeps_to_target": {k: v for k, v in res["sweeps_to_target"].items() if k != "warm"},
+                         "ms_to_target": res["ms_to_target"],
+                         "rmse_per_sweep": {k: [round(e, 5) for e in v] for k, v in res["curves"].items()
+                                            if k != "warm"}})
+    def med(key, sub):
+        vals = [d[key][sub] for d in per_seed if d[key][sub] is not None]
+        return float(statistics.median(vals)) if vals else None
+    runs = ("plain", "warm_p0", "warm_p1", "warm_p2")
+    out = {"metric": "sweeps and ms to the plain FP32 run's final test RMSE (x 1.001)", "workload":
+           f"zipf_100k shape (device-drawn), n_f={f}, lambda={lam}, r={r}, {sweeps} sweeps; nets "
+           f"{f + 2}-256-256-{f} GELU, trained 20 epochs on 5 seeds", "train_s": round(train_s, 1),
+           "train_loss_first_last": {k: [v[0], v[-1]] for k, v in hist.items()},
+           "median_sweeps": {k: med("sweeps_to_target", k) for k in runs},
+           "median_ms": {k: med("ms_to_target", k) for k in runs},
+           "runs": {"plain": "FP32 from random M^(0)", "warm_p0": "warm start, FP32",
+                    "warm_p1": "warm start, TF32 + 1 refinement", "warm_p2": "warm start, BF16 + 2 refinements"},
+           "per_seed": per_seed}
+    print(json.dumps(out), flush=True)
+
+
 def capture_arm(args):
     """Three half-sweeps of a small single-bucket case (a kernel capture
     takes the second launch with -s 1 -c 1)."""
@@ -513,6 +563,9 @@ def main():
     args = parse()
     if args.capture_case:
         capture_arm(args)
+        return 0
+    if args.workload == "warmstart":
+        warmstart_arm(args)
         return 0
     if args.workload == "zipf_1m":
         large_arm(args)

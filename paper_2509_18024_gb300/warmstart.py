@@ -28,10 +28,23 @@ class Pair:
     items: core_als.MLP
 
 
+def device_sides(problem):
+    """(Ru, Ri, (test_u, test_m, test_r)) on the device, for a host problem
+    (synth.RatingProblem) or one drawn on the device (synth.DeviceRatingProblem)."""
+    if hasattr(problem, "train_rows"):
+        Ru = core_als.DeviceCSR.from_host(problem.train_rows)
+        Ri = core_als.DeviceCSR.from_host(problem.train_cols)
+        test = tuple(torch.as_tensor(a).cuda() for a in (problem.test_u, problem.test_m, problem.test_r))
+    else:
+        Ru = core_als.DeviceCSR(problem.n_u, problem.n_m, *problem.rows)
+        Ri = core_als.DeviceCSR(problem.n_m, problem.n_u, *problem.cols)
+        test = (problem.test_u, problem.test_m, problem.test_r)
+    return Ru, Ri, test
+
+
 def converged_factors(problem, n_f, lam, budget, M0, sweeps, precision=0, gram_mode="asym"):
     """ALS from M0 for `sweeps` sweeps; returns device (U, M, Ru, Ri)."""
-    Ru = core_als.DeviceCSR.from_host(problem.train_rows)
-    Ri = core_als.DeviceCSR.from_host(problem.train_cols)
+    Ru, Ri, _ = device_sides(problem)
     eng = core_als.CoreALS(n_f, lam, budget, gram_mode=gram_mode, precision=precision)
     U, M, _ = eng.fit(Ru, Ri, torch.as_tensor(M0).cuda(), sweeps)
     return U, M, Ru, Ri
@@ -71,24 +84,33 @@ def warm_factor(nets: Pair, Ru, Ri, M0: torch.Tensor, n_f: int):
     return nets.items.forward(core_als.features(Ri, Uw, n_f))
 
 
-def judge(nets: Pair, problem, n_f, lam, budget, M0, sweeps, target=None):
-    """Test RMSE per sweep from M^(0) and from the warm start, the chosen start
-    (warm unless its first-sweep RMSE is worse) and the sweeps each needs to
-    reach `target` (default: the plain run's final RMSE x (1 + 1e-3))."""
-    Ru = core_als.DeviceCSR.from_host(problem.train_rows)
-    Ri = core_als.DeviceCSR.from_host(problem.train_cols)
-    test = tuple(torch.as_tensor(a).cuda() for a in (problem.test_u, problem.test_m, problem.test_r))
+def judge(nets: Pair, problem, n_f, lam, budget, M0, sweeps, target=None, precisions=(0,)):
+    """Test RMSE per sweep from M^(0) (plain ALS, FP32) and from the warm start
+    (one run per precision in `precisions`), the chosen start (warm unless its
+    first-sweep RMSE is worse) and the sweeps and CUDA-event milliseconds each
+    run needs to reach `target` (default: the plain run's final RMSE x
+    (1 + 1e-3)). A warm run's time includes computing the warm start."""
+    Ru, Ri, test = device_sides(problem)
     M0d = torch.as_tensor(M0).cuda()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    warm_factor(nets, Ru, Ri, M0d, n_f)  # first call builds the feature plans
+    torch.cuda.synchronize()
+    a.record()
     Mw = warm_factor(nets, Ru, Ri, M0d, n_f)
+    b.record()
+    torch.cuda.synchronize()
+    warm_ms = a.elapsed_time(b)
+    runs = [("plain", M0d, 0, 0.0)] + [(f"warm_p{prec}", Mw, prec, warm_ms) for prec in precisions]
     curves, times = {}, {}
-    for name, start in (("plain", M0d), ("warm", Mw)):
-        eng = core_als.CoreALS(n_f, lam, budget)
+    for name, start, prec, t0 in runs:
+        eng = core_als.CoreALS(n_f, lam, budget, precision=prec)
+        eng.prepare(Ru)
+        eng.prepare(Ri)
         M = start.clone()
         U = torch.empty((problem.n_u, n_f), device="cuda")
         errs, ms = [], []
-        total = 0.0
+        total = t0
         for _ in range(sweeps):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
             eng.sweep(Ru, Ri, U, M)
             b.record()
@@ -97,9 +119,15 @@ def judge(nets: Pair, problem, n_f, lam, budget, M0, sweeps, target=None):
             ms.append(total)
             errs.append(eng.rmse(*test, U, M))
         curves[name], times[name] = errs, ms
+        eng.close()
     if target is None:
         target = curves["plain"][-1] * (1 + 1e-3)
-    chosen = "warm" if curves["warm"][0] <= curves["plain"][0] else "plain"
+    first_warm = f"warm_p{precisions[0]}"
+    chosen = "warm" if curves[first_warm][0] <= curves["plain"][0] else "plain"
     reach = {k: next((q + 1 for q, e in enumerate(v) if e <= target), None) for k, v in curves.items()}
     reach_ms = {k: (times[k][reach[k] - 1] if reach[k] else None) for k in curves}
-    return {"target": target, "curves": curves, "chosen": chosen, "sweeps_to_target": reach, "ms_to_target": reach_ms}
+    out = {"target": target, "curves": curves, "chosen": chosen, "sweeps_to_target": reach,
+           "ms_to_target": reach_ms, "warm_start_ms": warm_ms}
+    out["curves"]["warm"] = curves[first_warm]
+    out["sweeps_to_target"]["warm"] = reach[first_warm]
+    return out

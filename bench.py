@@ -53,9 +53,10 @@ def parse():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--precision", choices=["fp32", "tf32", "bf16", "fp32_tc"], default="fp32")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--workload", choices=["zipf_100k", "zipf_1m", "warmstart"], default="zipf_100k",
+    ap.add_argument("--workload", choices=["zipf_100k", "zipf_1m", "warmstart", "batch64"], default="zipf_100k",
                     help="zipf_1m: the 1M x 100k, 10^8-cell matrix drawn on the device, fitted at --nf; "
-                         "warmstart: the learned warm start on 100k x 20k matrices (5 training, 5 held-out seeds)")
+                         "warmstart: the learned warm start on 100k x 20k matrices (5 training, 5 held-out seeds); "
+                         "batch64: 64 independent problems of mixed sizes and widths in one batch")
     ap.add_argument("--nf", type=int, default=None,
                     help="model width for --workload zipf_1m (default 64) or --capture-case (default 32)")
     ap.add_argument("--capture-case", choices=sorted(synth.CAPTURE_CASES), default=None,
@@ -540,6 +541,79 @@ def warmstart_arm(args):
     print(json.dumps(out), flush=True)
 
 
+def batch_arm(args):
+    """64 independent completion problems fitted as one batch (one sweep of
+    all width groups replayed as a CUDA graph), against fitting them one by
+    one. Problem q: t ~ U(0, 1), n_u = 500 * 100^t, n_m = 300 * (100/3)^t,
+    density log-uniform in [0.5 %, 10 %] (capped at 4 * 10^6 cells), n_f
+    uniform over {8, 16, 32, 64, 128}, Zipf(0.9) cells, ratings as the
+    100k x 20k workload (rank-32 truth), drawn on the device; r = 0.25."""
+    import torch
+    from paper_2509_18024_gb300 import core_als
+    rng = np.random.default_rng(args.seed)
+    r = args.budget if args.budget is not None else 0.25
+    prec = PRECISIONS[args.precision]
+    specs, problems = [], []
+    for q in range(64):
+        t = rng.random()
+        n_u, n_m = int(round(500 * 100 ** t)), int(round(300 * (100 / 3) ** t))
+        dens = float(np.exp(rng.uniform(np.log(0.005), np.log(0.1))))
+        nnz = max(1000, min(int(n_u * n_m * dens), 4_000_000))
+        f = int(rng.choice([8, 16, 32, 64, 128]))
+        d = synth.zipf_ratings_device(n_u, n_m, 32, nnz, 0.9, 0.5, 3000 + q)
+        Ru = core_als.DeviceCSR(n_u, n_m, *d.rows)
+        Ri = core_als.DeviceCSR(n_m, n_u, *d.cols)
+        specs.append((n_u, n_m, nnz, f))
+        problems.append((Ru, Ri, f, torch.empty((n_u, f), device="cuda"),
+                         torch.as_tensor(synth.init_factor(n_m, f, 4000 + q)).cuda()))
+    rows = sum(a + b for a, b, _, _ in specs)
+    batch = core_als.CoreBatch(problems, 0.05, r, precision=prec)
+    batch.fit(args.warmup).synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(batch.stream):
+        a.record()
+        batch.fit(args.steps)
+        b.record()
+    batch.synchronize()
+    ms_batch = a.elapsed_time(b) / args.steps
+    launches = batch.launches_per_sweep
+    batch.close()
+    # The same problems one by one (a handle per width, sweeps issued in turn).
+    engines = {}
+    for (Ru, Ri, f, U, M) in problems:
+        if f not in engines:
+            engines[f] = core_als.CoreALS(f, 0.05, r, precision=prec)
+        engines[f].prepare(Ru)
+        engines[f].prepare(Ri)
+    for (Ru, Ri, f, U, M) in problems:
+        engines[f].sweep(Ru, Ri, U, M)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(args.steps):
+        for (Ru, Ri, f, U, M) in problems:
+            engines[f].sweep(Ru, Ri, U, M)
+    b.record()
+    torch.cuda.synchronize()
+    ms_seq = a.elapsed_time(b) / args.steps
+    by_f = {}
+    for n_u, n_m, nnz, f in specs:
+        e = by_f.setdefault(f, [0, 0, 0])
+        e[0] += 1
+        e[1] += n_u + n_m
+        e[2] += nnz
+    out = {"metric": METRIC, "value": rows / (ms_batch / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_batch, "higher_is_better": True, "dtype": args.precision,
+           "data": "synthetic (device-drawn Zipf)",
+           "config": {"workload": "batch64: 64 independent problems, 500x300 .. 50kx10k, n_f in {8,16,32,64,128}, "
+                                  f"density 0.5-10 %, Zipf 0.9, r={r}", "problems": 64, "row_solves_per_sweep": rows,
+                      "cells": int(sum(s[2] for s in specs)),
+                      "by_n_f": {str(k): {"problems": v[0], "rows": v[1], "cells": v[2]} for k, v in sorted(by_f.items())}},
+           "batched_graph": {"ms_per_sweep": ms_batch, "launches_per_sweep": launches},
+           "one_by_one": {"ms_per_sweep": ms_seq, "row_solves_per_s": rows / (ms_seq / 1e3)},
+           "speedup_of_batching": ms_seq / ms_batch}
+    print(json.dumps(out), flush=True)
+
+
 def capture_arm(args):
     """Three half-sweeps of a small single-bucket case (a kernel capture
     takes the second launch with -s 1 -c 1)."""
@@ -566,6 +640,9 @@ def main():
         return 0
     if args.workload == "warmstart":
         warmstart_arm(args)
+        return 0
+    if args.workload == "batch64":
+        batch_arm(args)
         return 0
     if args.workload == "zipf_1m":
         large_arm(args)

@@ -256,14 +256,20 @@ def zipf_ratings_device(n_u: int, n_m: int, f: int, nnz: int, zipf_s: float, noi
         return torch.cumsum(w / w.sum(), 0)
 
     cu, cm = cdf(n_u), cdf(n_m)
+    if nnz > n_u * n_m:
+        raise ValueError("more cells requested than the matrix holds")
     have = torch.empty(0, dtype=torch.int64, device=device)
-    while have.numel() < nnz:
+    for _ in range(1000):
+        if have.numel() >= nnz:
+            break
         want = int((nnz - have.numel()) * 1.3) + 1024
         i = torch.clamp(torch.searchsorted(cu, torch.rand(want, generator=g, device=device, dtype=torch.float64)),
                         max=n_u - 1)
         j = torch.clamp(torch.searchsorted(cm, torch.rand(want, generator=g, device=device, dtype=torch.float64)),
                         max=n_m - 1)
         have = torch.unique(torch.cat([have, i * n_m + j]))
+    if have.numel() < nnz:
+        raise ValueError("the popularity law leaves too few distinct cells for nnz")
     keep = torch.randperm(have.numel(), generator=g, device=device)[:nnz]
     cells = have[torch.sort(keep).values]
     del have, keep

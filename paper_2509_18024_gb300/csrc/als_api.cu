@@ -511,11 +511,12 @@ int launch_split(als_handle* h, const Plan& pl, const Side& side, const Params& 
     split_views(pl, F, sp, ss);
     const int sc = pl.n_slots * F;
     ALS_LAUNCH(h, "split_init", als::k_split_init<F><<<(sc + 255) / 256, 256, 0, st>>>(side, p, sp, ss));
-    const size_t hsmem = (size_t)F * als::kHistRow * 4;
+    constexpr int CG = als::split_hist_cols(F);
+    const size_t hsmem = (size_t)CG * als::kHistRow * 4;
     ALS_CUDA(h, cudaFuncSetAttribute(als::k_split_hist<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem));
     for (int pass = 0; pass < 4; ++pass) {
-        ALS_LAUNCH(h, "split_hist",
-                   als::k_split_hist<F><<<pl.n_super, als::kCtaThreads, hsmem, st>>>(side, p, sp, ss, pass));
+        ALS_LAUNCH(h, "split_hist", als::k_split_hist<F><<<pl.n_super * (F / CG), als::kCtaThreads, hsmem, st>>>(
+                                        side, p, sp, ss, pass));
     }
     ALS_LAUNCH(h, "split_eqcount", als::k_split_eqcount<F><<<pl.n_chunks, als::kCtaThreads, 0, st>>>(side, p, sp, ss));
     ALS_LAUNCH(h, "split_cut", als::k_split_cut<F><<<(sc * 32 + 255) / 256, 256, 0, st>>>(side, p, sp, ss));

@@ -28,6 +28,13 @@ struct SplitChunk {
 };
 __host__ __device__ constexpr int split_chunk(int F) { return F <= 32 ? 512 : (F == 64 ? 256 : 128); }
 
+// Columns per histogram CTA of a split row (its shared bins: 32 x 265 words).
+template <int F>
+struct SplitHistCols {
+    static constexpr int value = F < 32 ? F : 32;
+};
+__host__ __device__ constexpr int split_hist_cols(int F) { return F < 32 ? F : 32; }
+
 // Mask words per position.
 template <int F>
 struct MaskWords {
@@ -625,21 +632,26 @@ __global__ void __launch_bounds__(kCtaThreads) k_split_hist(Side side, Params p,
                                                             int pass) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     uint32_t (*hist)[kHistRow] = reinterpret_cast<uint32_t (*)[kHistRow]>(smem_raw);
+    constexpr int CG = SplitHistCols<F>::value;  // columns of this CTA's group
+    constexpr int NG = F / CG;
     const int tid = threadIdx.x;
-    const int slot = sp.sc_slot[blockIdx.x];
+    const int sc = blockIdx.x / NG, grp = blockIdx.x % NG;
+    const int slot = sp.sc_slot[sc];
     const int64_t row = sp.row[slot];
     const int64_t lo = side.indptr[row];
     const int n = (int)(side.indptr[row + 1] - lo);
-    const int start = sp.sc_start[blockIdx.x];
+    const int start = sp.sc_start[sc];
     const int len = min(kSplitSuper, n - start);
-    for (int e = tid; e < F * kHistRow; e += kCtaThreads) (&hist[0][0])[e] = 0u;
+    for (int e = tid; e < CG * kHistRow; e += kCtaThreads) (&hist[0][0])[e] = 0u;
     __syncthreads();
-    // Thread (k, q) covers columns 4q..4q+3 of positions k0, k0 + kstep, ...:
-    // one index load and one float4 gather (f == F, aligned Y) per position.
-    constexpr int T4 = F / 4;
+    // Thread (k, q) covers columns 4q..4q+3 of its group of positions k0,
+    // k0 + kstep, ...: one index load and one float4 gather (f == F, aligned
+    // Y) per position.
+    constexpr int T4 = CG / 4;
     constexpr int kstep = kCtaThreads / T4;
     const int q = tid % T4, k0 = tid / T4;
-    const int sa = slot * F + 4 * q;
+    const int col0 = grp * CG + 4 * q;  // first column of this thread
+    const int sa = slot * F + col0;
     bool open[4];
     uint32_t Pc[4];
     bool any = false;
@@ -668,10 +680,10 @@ __global__ void __launch_bounds__(kCtaThreads) k_split_hist(Side side, Params p,
                 if (j[u] < 0) {
                     v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
                 } else if (vec) {
-                    v[u] = __ldg(reinterpret_cast<const float4*>(side.Y + (int64_t)j[u] * F) + q);
+                    v[u] = __ldg(reinterpret_cast<const float4*>(side.Y + (int64_t)j[u] * F + col0));
                 } else {
                     const float* y = side.Y + (int64_t)j[u] * f;
-                    const int a = 4 * q;
+                    const int a = col0;
                     v[u] = make_float4(a < f ? __ldg(y + a) : 0.f, a + 1 < f ? __ldg(y + a + 1) : 0.f,
                                        a + 2 < f ? __ldg(y + a + 2) : 0.f, a + 3 < f ? __ldg(y + a + 3) : 0.f);
                 }
@@ -689,8 +701,8 @@ __global__ void __launch_bounds__(kCtaThreads) k_split_hist(Side side, Params p,
         }
     }
     __syncthreads();
-    uint32_t* g = st.ghist + (int64_t)slot * F * 256;
-    for (int e = tid; e < F * 256; e += kCtaThreads) {
+    uint32_t* g = st.ghist + ((int64_t)slot * F + grp * CG) * 256;
+    for (int e = tid; e < CG * 256; e += kCtaThreads) {
         const uint32_t v = hist[e >> 8][hist_slot(e & 255)];
         if (v) atomicAdd(g + e, v);
     }
@@ -701,7 +713,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_split_hist(Side side, Params p,
     __shared__ int last;
     __threadfence();
     __syncthreads();
-    if (tid == 0) last = atomicAdd(st.arrive + slot, 1) == (n + kSplitSuper - 1) / kSplitSuper - 1;
+    if (tid == 0) last = atomicAdd(st.arrive + slot, 1) == NG * ((n + kSplitSuper - 1) / kSplitSuper) - 1;
     __syncthreads();
     if (!last) return;
     __threadfence();

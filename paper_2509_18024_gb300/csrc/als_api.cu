@@ -284,7 +284,8 @@ double* eval_partials(als_handle* h) {
 }
 double* eval_out(als_handle* h) { return eval_partials(h) + als::kEvalBlocks; }
 unsigned* valid_err(als_handle* h) { return reinterpret_cast<unsigned*>(eval_out(h) + 1); }
-constexpr size_t kMiscBytes = 256 + (als::kEvalBlocks + 1) * sizeof(double) + 64;
+constexpr size_t kColmaxOffset = 256 + (als::kEvalBlocks + 1) * sizeof(double) + 64;  // uint32[128]
+constexpr size_t kMiscBytes = kColmaxOffset + 128 * sizeof(uint32_t);
 
 // Validate one side's structure on the device and download its indptr.
 int validate_csr(als_handle* h, const als_csr* R, std::vector<int64_t>& indptr) {
@@ -460,7 +461,7 @@ int tc_launch_shape(als_handle* h, K kernel, size_t smem, int eng, uint32_t tmem
 
 template <int F, int NS, int ENG>
 int launch_cta_bucket(als_handle* h, const Side& side, const Params& p, const int32_t* list, int count, int mode,
-                      float* G_aug, uint32_t* masks_out) {
+                      float* G_aug, uint32_t* masks_out, const uint32_t* tcol) {
     if (count == 0) return ALS_OK;
     auto kern = als::k_cta_rows<F, NS, ENG>;
     size_t smem = sizeof(als::CtaSmem<F, NS, ENG>);
@@ -472,7 +473,7 @@ int launch_cta_bucket(als_handle* h, const Side& side, const Params& p, const in
         if (rc) return rc;
     }
     ALS_LAUNCH(h, "cta_rows", kern<<<grid, als::kCtaThreads, smem, h->stream>>>(side, p, list, count, mode, G_aug,
-                                                                              masks_out));
+                                                                              masks_out, tcol));
     return ALS_OK;
 }
 
@@ -619,14 +620,22 @@ int run_side(als_handle* h, const Plan& pl, const Side& side, int mode, float* X
     rc = launch_split<F, ENG>(h, pl, side, p, mode, aug_split, masks_out);
     if (rc) return rc;
     const int32_t* lists = pl.d_lists;
+    // Largest exponent per factor column: the top of the resident rows' CES window.
+    uint32_t* tcol = reinterpret_cast<uint32_t*>(static_cast<char*>(h->misc.p) + kColmaxOffset);
+    if (pl.n_bucket[0] + pl.n_bucket[1] + pl.n_bucket[2] > 0) {
+        ALS_CUDA(h, cudaMemsetAsync(tcol, 0, (size_t)F * sizeof(uint32_t), st));
+        const int64_t total = side.n_cols * (int64_t)p.f;
+        const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)h->n_sm * 4));
+        ALS_LAUNCH(h, "colmax", als::k_colmax<F><<<blocks, 256, 0, st>>>(side.Y, side.n_cols, p.f, tcol));
+    }
     rc = launch_cta_bucket<F, Caps<F>::c2, ENG>(h, side, p, lists + pl.off_bucket(2), pl.n_bucket[2], mode, aug_b2,
-                                               masks_out);
+                                               masks_out, tcol);
     if (rc) return rc;
     rc = launch_cta_bucket<F, Caps<F>::c1, ENG>(h, side, p, lists + pl.off_bucket(1), pl.n_bucket[1], mode, aug_b1,
-                                               masks_out);
+                                               masks_out, tcol);
     if (rc) return rc;
     rc = launch_cta_bucket<F, Caps<F>::c0, ENG>(h, side, p, lists + pl.off_bucket(0), pl.n_bucket[0], mode, aug_b0,
-                                               masks_out);
+                                               masks_out, tcol);
     if (rc) return rc;
     if constexpr (F <= 32) {
         if (n_warp > 0)

@@ -260,13 +260,41 @@ __device__ __forceinline__ void gram_tile(uint8_t* scratch, uint64_t*, uint32_t*
 }
 
 // ---------------------------------------------------------------------------
+// Largest exponent of |y_a| over every row of the factor Y (n_cols x f), per
+// column: tcol[a] (zeroed before the launch). The CES window of a row starts
+// one above it.
+template <int F>
+__global__ void k_colmax(const float* __restrict__ Y, int64_t n_cols, int f, uint32_t* __restrict__ tcol) {
+    __shared__ uint32_t m[F];
+    for (int a = threadIdx.x; a < F; a += blockDim.x) m[a] = 0u;
+    __syncthreads();
+    const int64_t total = n_cols * f;
+    uint32_t local = 0u;
+    int la = -1;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(e % f);
+        if (a != la) {
+            if (la >= 0) atomicMax(&m[la], local);
+            la = a;
+            local = 0u;
+        }
+        local = max(local, mag_key(Y[e]) >> 23);
+    }
+    if (la >= 0) atomicMax(&m[la], local);
+    __syncthreads();
+    for (int a = threadIdx.x; a < f; a += blockDim.x)
+        if (m[a]) atomicMax(&tcol[a], m[a]);
+}
+
+// ---------------------------------------------------------------------------
 // CES of a resident slice, one warp per quad of 4 columns (Algorithm 1 per
 // column: the s largest |x_ka|, ties to the lower position), by an exact
 // radix select on the magnitude keys with 64 bins per column and pass:
 //   window pass: keys whose exponent E lies in [T - 16, T) go to bin
 //     ((E - T + 16) << 2) | key bits 22..21 (quarter octaves). T starts one
-//     above the column's largest exponent; if the window holds fewer than
-//     `need` keys, they are all kept and the window moves down (T -= 16).
+//     above the largest exponent of the factor's column (over all its rows);
+//     if the window holds fewer than `need` keys, they are all kept and the
+//     window moves down (T -= 16).
 //   mantissa passes: key bits 20..15, 14..9, 8..3, 2..0 of the keys equal to
 //     the prefix P on the bits resolved so far (mask Mk).
 // A column is done when the bin holding the need-th key is taken whole;
@@ -333,7 +361,8 @@ __device__ __forceinline__ uint32_t quad_scan(uint32_t* H, bool act, uint32_t ne
 // kQuadHistWords bins, all zero on entry and on return.
 template <int F>
 __device__ __forceinline__ void quad_select(const float (*x)[xpitch(F)], int n, int f, long long s, int q, uint32_t* H,
-                                            uint32_t* P_out, uint32_t* Mk_out, int32_t* cut_out) {
+                                            const uint32_t* __restrict__ tcol, uint32_t* P_out, uint32_t* Mk_out,
+                                            int32_t* cut_out) {
     const int lane = threadIdx.x & 31;
     uint32_t P[4], Mk[4];
     int need[4], cut[4], T[4];
@@ -347,18 +376,10 @@ __device__ __forceinline__ void quad_select(const float (*x)[xpitch(F)], int n, 
     }
     const float4* xq = reinterpret_cast<const float4*>(&x[0][4 * q]);
     constexpr int XQ = xpitch(F) / 4;  // float4 per tile row
-    if (open[0] || open[1] || open[2] || open[3]) {
-        uint32_t em[4] = {0u, 0u, 0u, 0u};
-        for (int k = lane; k < n; k += 32) {
-            const float4 v = xq[k * XQ];
-            em[0] = max(em[0], mag_key(v.x) >> 23);
-            em[1] = max(em[1], mag_key(v.y) >> 23);
-            em[2] = max(em[2], mag_key(v.z) >> 23);
-            em[3] = max(em[3], mag_key(v.w) >> 23);
-        }
+    // Window tops: one above the factor column's largest exponent (no key
+    // of this row is above it).
 #pragma unroll
-        for (int c = 0; c < 4; ++c) T[c] = (int)__reduce_max_sync(kFull, em[c]) + 1;
-    }
+    for (int c = 0; c < 4; ++c) T[c] = (int)tcol[4 * q + c] + 1;
     // Bin b (< 64) of column c sits at word c * kQuadPitch + b + ((b >> 3) & 4).
     // Window passes (at most 16 windows of 16 exponents cover all 256).
     for (int it = 0; it < 16; ++it) {
@@ -492,7 +513,8 @@ struct CtaSmem {
 template <int F, int NS, int ENG>
 __global__ void __launch_bounds__(kCtaThreads, ENG == ENG_CUDA ? 4 : 1) k_cta_rows(Side side, Params p, const int32_t* __restrict__ rows,
                                                           int n_list, int mode, float* __restrict__ G_aug,
-                                                          uint32_t* __restrict__ masks_out) {
+                                                          uint32_t* __restrict__ masks_out,
+                                                          const uint32_t* __restrict__ tcol) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     using Smem = CtaSmem<F, NS, ENG>;
     Smem& S = *reinterpret_cast<Smem*>(smem_raw);
@@ -532,7 +554,7 @@ __global__ void __launch_bounds__(kCtaThreads, ENG == ENG_CUDA ? 4 : 1) k_cta_ro
         uint32_t* H = reinterpret_cast<uint32_t*>(S.u) + warp * kQuadHistWords;
         for (int e = lane; e < kQuadHistWords / 4; e += 32) reinterpret_cast<uint4*>(H)[e] = make_uint4(0u, 0u, 0u, 0u);
         __syncwarp();
-        for (int q = warp; q < F / 4; q += kCtaWarps) quad_select<F>(S.x, n, f, s, q, H, S.P, S.Mk, S.cut);
+        for (int q = warp; q < F / 4; q += kCtaWarps) quad_select<F>(S.x, n, f, s, q, H, tcol, S.P, S.Mk, S.cut);
     }
     __syncthreads();
     build_masks<F>(S.mask, S.x, n, 0, S.P, S.Mk, S.cut);

@@ -717,12 +717,16 @@ __global__ void __launch_bounds__(kEvalThreads) k_sse(int64_t n, const int32_t* 
     if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
 }
 
+// One warp: lane l sums partials l, l + 32, ... in order, then a fixed
+// butterfly adds the lanes (the same order every run).
 __global__ void k_sum_partials(const double* __restrict__ partials, int n, double* __restrict__ out) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s = 0.0;
-        for (int q = 0; q < n; ++q) s += partials[q];
-        *out = s;
-    }
+    const int lane = threadIdx.x & 31;
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+    double s = 0.0;
+    for (int q = lane; q < n; q += 32) s += partials[q];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    if (lane == 0) *out = s;
 }
 
 __global__ void k_zero_rows(const int32_t* __restrict__ rows, int n_list, int f, float* __restrict__ X_out) {

@@ -452,6 +452,99 @@ struct RegSolve {
     static constexpr size_t SMEM = (size_t)F * P * sizeof(float);
 };
 
+// One block of 8 elimination steps of k_solve_reg (block t: columns 8t ..
+// 8t + 7 in registers 0..7), then the left shift by 8. NCHB bounds the float4
+// chunks that can still hold live columns in this block (compile-time, so
+// that later blocks skip the dead tail without runtime tests).
+template <int F, int NCHB>
+__device__ __forceinline__ void reg_lu_block(float (&r)[F + 1], const int t, bool& live, const bool pivot,
+                                             float (*U)[F + 4], uint32_t (*s_key)[F / 32], int (*s_idx)[F / 32],
+                                             float* s_pv, float* s_dinv, int* s_ord, const int store, float* src) {
+    constexpr int NW = F / 32, R = F + 1;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int rem = R - 8 * t;  // registers still holding columns 8t .. F
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        const int k = 8 * t + s;
+        uint32_t key;
+        if (pivot) key = live ? __float_as_uint(fabsf(r[s])) + 1u : 0u;
+        else key = tid == k ? 1u : 0u;
+        const uint32_t m = __reduce_max_sync(kFull, key);
+        const unsigned bal = __ballot_sync(kFull, key == m && m != 0u);
+        if (lane == 0) {
+            s_key[k & 1][warp] = m;
+            s_idx[k & 1][warp] = bal ? warp * 32 + __ffs(bal) - 1 : F;
+        }
+        __syncthreads();
+        uint32_t bm = 0u;
+        int pidx = F;
+#pragma unroll
+        for (int v = 0; v < NW; ++v) {
+            const uint32_t kv = s_key[k & 1][v];
+            const int iv = s_idx[k & 1][v];
+            if (kv > bm || (kv == bm && iv < pidx)) {
+                bm = kv;
+                pidx = iv;
+            }
+        }
+        if (tid == pidx) {
+            float* urow = &U[k][8 * t];
+#pragma unroll
+            for (int c = 0; c < NCHB; ++c) {
+                if (4 * c < rem) {
+                    if (4 * c + 3 < R) {
+                        *reinterpret_cast<float4*>(urow + 4 * c) = make_float4(r[4 * c], r[4 * c + 1], r[4 * c + 2], r[4 * c + 3]);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (4 * c + e < R) urow[4 * c + e] = r[4 * c + e];
+                    }
+                }
+            }
+            const float pv = r[s];
+            s_pv[k] = pv;
+            s_dinv[k] = pv != 0.f ? 1.0f / pv : 0.f;
+            s_ord[k] = tid;
+            live = false;
+        }
+        __syncthreads();
+        const float di = s_dinv[k];
+        if (live && di != 0.f) {
+            const float l = r[s] * di;
+            r[s] = l;
+            const float* urow = &U[k][8 * t];
+#pragma unroll
+            for (int c = (s + 1) / 4; c < NCHB; ++c) {
+                if (4 * c < rem) {
+                    float u4[4];
+                    if (4 * c + 3 < R) {
+                        const float4 v = *reinterpret_cast<const float4*>(urow + 4 * c);
+                        u4[0] = v.x;
+                        u4[1] = v.y;
+                        u4[2] = v.z;
+                        u4[3] = v.w;
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) u4[e] = (4 * c + e < R) ? urow[4 * c + e] : 0.f;
+                    }
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int j = 4 * c + e;
+                        if (j > s && j < R) r[j] = fmaf(-l, u4[e], r[j]);
+                    }
+                }
+            }
+        }
+    }
+    if (store) {
+        float* dst = src + (int64_t)tid * (F + 1) + 8 * t;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) dst[e] = r[e];
+    }
+#pragma unroll
+    for (int j = 0; j + 8 < R; ++j) r[j] = r[j + 8];
+}
+
 template <int F>
 __global__ void __launch_bounds__(RegSolve<F>::NT, F == 64 ? 8 : 2) k_solve_reg(
     float* __restrict__ G_aug, const int32_t* __restrict__ rows, int n_list, Params p, float* __restrict__ X_out,
@@ -478,88 +571,22 @@ __global__ void __launch_bounds__(RegSolve<F>::NT, F == 64 ? 8 : 2) k_solve_reg(
     __syncthreads();
     const bool pivot = p.gram_mode == GRAM_ASYM;
     bool live = true;
-    for (int t = 0; t < F / 8; ++t) {
-        const int rem = R - 8 * t;  // registers still holding columns 8t .. F
-#pragma unroll
-        for (int s = 0; s < 8; ++s) {
-            const int k = 8 * t + s;
-            uint32_t key;
-            if (pivot) key = live ? __float_as_uint(fabsf(r[s])) + 1u : 0u;
-            else key = tid == k ? 1u : 0u;
-            const uint32_t m = __reduce_max_sync(kFull, key);
-            const unsigned bal = __ballot_sync(kFull, key == m && m != 0u);
-            if (lane == 0) {
-                s_key[k & 1][warp] = m;
-                s_idx[k & 1][warp] = bal ? warp * 32 + __ffs(bal) - 1 : F;
-            }
-            __syncthreads();
-            uint32_t bm = 0u;
-            int pidx = F;
-#pragma unroll
-            for (int v = 0; v < NW; ++v) {
-                const uint32_t kv = s_key[k & 1][v];
-                const int iv = s_idx[k & 1][v];
-                if (kv > bm || (kv == bm && iv < pidx)) {
-                    bm = kv;
-                    pidx = iv;
-                }
-            }
-            if (tid == pidx) {
-                float* urow = &U[k][8 * t];
-#pragma unroll
-                for (int c = 0; c < C::NCH; ++c) {
-                    if (4 * c < rem) {
-                        if (4 * c + 3 < R) {
-                            *reinterpret_cast<float4*>(urow + 4 * c) = make_float4(r[4 * c], r[4 * c + 1], r[4 * c + 2], r[4 * c + 3]);
-                        } else {
-#pragma unroll
-                            for (int e = 0; e < 4; ++e)
-                                if (4 * c + e < R) urow[4 * c + e] = r[4 * c + e];
-                        }
-                    }
-                }
-                const float pv = r[s];
-                s_pv[k] = pv;
-                s_dinv[k] = pv != 0.f ? 1.0f / pv : 0.f;
-                s_ord[k] = tid;
-                live = false;
-            }
-            __syncthreads();
-            const float di = s_dinv[k];
-            if (live && di != 0.f) {
-                const float l = r[s] * di;
-                r[s] = l;
-                const float* urow = &U[k][8 * t];
-#pragma unroll
-                for (int c = (s + 1) / 4; c < C::NCH; ++c) {
-                    if (4 * c < rem) {
-                        float u4[4];
-                        if (4 * c + 3 < R) {
-                            const float4 v = *reinterpret_cast<const float4*>(urow + 4 * c);
-                            u4[0] = v.x;
-                            u4[1] = v.y;
-                            u4[2] = v.z;
-                            u4[3] = v.w;
-                        } else {
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) u4[e] = (4 * c + e < R) ? urow[4 * c + e] : 0.f;
-                        }
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const int j = 4 * c + e;
-                            if (j > s && j < R) r[j] = fmaf(-l, u4[e], r[j]);
-                        }
-                    }
-                }
-            }
-        }
-        if (store) {
-            float* dst = src + (int64_t)tid * (F + 1) + 8 * t;
-#pragma unroll
-            for (int e = 0; e < 8; ++e) dst[e] = r[e];
-        }
-#pragma unroll
-        for (int j = 0; j + 8 < R; ++j) r[j] = r[j + 8];
+    // n_f = 128: four quarters of the elimination, each with the chunk bound
+    // of its first block (the live width shrinks by 8 columns per block). At
+    // n_f = 64 one bound for all blocks keeps the kernel within its registers.
+    constexpr int QB = F / 32;  // blocks per quarter
+    if constexpr (F < 128) {
+        for (int t = 0; t < F / 8; ++t)
+            reg_lu_block<F, (R + 3) / 4>(r, t, live, pivot, U, s_key, s_idx, s_pv, s_dinv, s_ord, store, src);
+    } else {
+    for (int t = 0; t < QB; ++t)
+        reg_lu_block<F, (R + 3) / 4>(r, t, live, pivot, U, s_key, s_idx, s_pv, s_dinv, s_ord, store, src);
+    for (int t = QB; t < 2 * QB; ++t)
+        reg_lu_block<F, (R - 8 * QB + 3) / 4>(r, t, live, pivot, U, s_key, s_idx, s_pv, s_dinv, s_ord, store, src);
+    for (int t = 2 * QB; t < 3 * QB; ++t)
+        reg_lu_block<F, (R - 16 * QB + 3) / 4>(r, t, live, pivot, U, s_key, s_idx, s_pv, s_dinv, s_ord, store, src);
+    for (int t = 3 * QB; t < 4 * QB; ++t)
+        reg_lu_block<F, (R - 24 * QB + 3) / 4>(r, t, live, pivot, U, s_key, s_idx, s_pv, s_dinv, s_ord, store, src);
     }
     __syncthreads();
     bool singular = false;

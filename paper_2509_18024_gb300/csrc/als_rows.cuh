@@ -24,9 +24,9 @@ __host__ __device__ constexpr int tc_prec(int eng) { return eng == ENG_BF16 ? TC
 // Positions per Gram chunk of a split row, by padded width.
 template <int F>
 struct SplitChunk {
-    static constexpr int value = F <= 32 ? 512 : (F == 64 ? 256 : 128);
+    static constexpr int value = F <= 32 ? 256 : (F == 64 ? 256 : 128);
 };
-__host__ __device__ constexpr int split_chunk(int F) { return F <= 32 ? 512 : (F == 64 ? 256 : 128); }
+__host__ __device__ constexpr int split_chunk(int F) { return F <= 32 ? 256 : (F == 64 ? 256 : 128); }
 
 // Columns per histogram CTA of a split row (its shared bins: 32 x 265 words).
 template <int F>
@@ -231,21 +231,13 @@ __device__ __forceinline__ void build_masks(uint32_t (*mask)[MaskWords<F>::value
     }
 }
 
-// Masked Gram of positions [0, cn) of a staged tile on CUDA cores (FP32,
-// n_f <= 32). The result (no regulariser) goes to out(a, c, v) for a < F,
-// c <= F, called once per value by some thread. scratch: per-warp partials.
-template <int F, int ENG, class Out>
-__device__ __forceinline__ void gram_tile(uint8_t* scratch, uint64_t*, uint32_t*, const float (*x)[xpitch(F)],
-                                          const uint32_t (*mask)[MaskWords<F>::value], const float* r, int cn,
-                                          bool sym, Out out) {
-    static_assert(ENG == ENG_CUDA && F <= 32, "CUDA-core Gram is built for n_f <= 32");
+// The CTA's Gram from the warps' register partials: they meet in kGramBufs
+// shared buffers (warps w >= kGramBufs store, warps w < kGramBufs add theirs
+// into buffer w), then the buffers are summed in order into out(a, c, v).
+template <int F, class Out>
+__device__ __forceinline__ void gram_flush(uint8_t* scratch, const GramAcc<F>& g, Out out) {
     const int tid = threadIdx.x, warp = tid >> 5;
-    // Warp partials meet in kGramBufs buffers: warps w >= kGramBufs store,
-    // warps w < kGramBufs add theirs into buffer w, then the buffers are summed.
     float (*Gp)[F][F + 1] = reinterpret_cast<float (*)[F][F + 1]>(scratch);
-    GramAcc<F> g;
-    g.zero();
-    g.add_tile(x, &mask[0][0], r, warp, cn, kCtaWarps, sym);
     if (warp >= kGramBufs) g.template store<false>(Gp[warp - kGramBufs]);
     __syncthreads();
     if (warp < kGramBufs) g.template store<true>(Gp[warp]);
@@ -257,6 +249,21 @@ __device__ __forceinline__ void gram_tile(uint8_t* scratch, uint64_t*, uint32_t*
         for (int q = 0; q < kGramBufs; ++q) v += Gp[q][a][c];
         out(a, c, v);
     }
+}
+
+// Masked Gram of positions [0, cn) of a staged tile on CUDA cores (FP32,
+// n_f <= 32). The result (no regulariser) goes to out(a, c, v) for a < F,
+// c <= F, called once per value by some thread. scratch: per-warp partials.
+template <int F, int ENG, class Out>
+__device__ __forceinline__ void gram_tile(uint8_t* scratch, uint64_t*, uint32_t*, const float (*x)[xpitch(F)],
+                                          const uint32_t (*mask)[MaskWords<F>::value], const float* r, int cn,
+                                          bool sym, Out out) {
+    static_assert(ENG == ENG_CUDA && F <= 32, "CUDA-core Gram is built for n_f <= 32");
+    const int tid = threadIdx.x, warp = tid >> 5;
+    GramAcc<F> g;
+    g.zero();
+    g.add_tile(x, &mask[0][0], r, warp, cn, kCtaWarps, sym);
+    gram_flush<F>(scratch, g, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -835,11 +842,14 @@ struct SplitGramSmem {
     uint32_t tmem_slot;
 };
 
-// Masked Gram of split chunks into part[c] (or masks only when mode == 2);
-// persistent over chunks with a tensor-core engine (as k_cta_rows).
+// Masked Gram of split chunks (or masks only when mode == 2). Tensor-core
+// engines: persistent, chunks strided over the CTAs, one partial per chunk in
+// part[c]. CUDA cores: CTA b takes the contiguous chunks [b per, (b+1) per)
+// and keeps its register partials across consecutive chunks of one row; the
+// run's Gram goes to part[first chunk of the run] when the row changes.
 template <int F, int ENG>
 __global__ void __launch_bounds__(kCtaThreads) k_split_gram(Side side, Params p, SplitPlan sp, SplitState st,
-                                                            int mode, uint32_t* __restrict__ masks_out) {
+                                                            int mode, uint32_t* __restrict__ masks_out, int per) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     using Smem = SplitGramSmem<F, ENG>;
     Smem& S = *reinterpret_cast<Smem*>(smem_raw);
@@ -862,7 +872,13 @@ __global__ void __launch_bounds__(kCtaThreads) k_split_gram(Side side, Params p,
             prev_c = -1;
         }
     };
-    for (int c = blockIdx.x; c < sp.n_chunks; c += gridDim.x, ++iter) {
+    const int c_first = TC ? blockIdx.x : blockIdx.x * per;
+    const int c_end = TC ? sp.n_chunks : min(c_first + per, sp.n_chunks);
+    const int c_step = TC ? gridDim.x : 1;
+    GramAcc<F> acc;  // CUDA cores: the current run's warp partials
+    if constexpr (!TC) acc.zero();
+    int run_start = c_first;
+    for (int c = c_first; c < c_end; c += c_step, ++iter) {
         __syncthreads();
         const ChunkInfo ci = chunk_info<F>(sp, side, c);
         stage_tile<F>(S.x, S.r, S.idx, side, p.f, ci.lo + ci.start, ci.len);
@@ -879,9 +895,13 @@ __global__ void __launch_bounds__(kCtaThreads) k_split_gram(Side side, Params p,
             prev_acc = iter & 1;
             prev_len = ci.len;
         } else {
-            float* dst = st.part + (int64_t)c * F * (F + 1);
-            gram_tile<F, ENG>(S.u, nullptr, nullptr, S.x, S.mask, S.r, ci.len, sym,
-                              [&](int a, int cc, float v) { dst[a * (F + 1) + cc] = v; });
+            acc.add_tile(S.x, &S.mask[0][0], S.r, tid >> 5, ci.len, kCtaWarps, sym);
+            if (c + 1 == c_end || sp.ch_slot[c + 1] != ci.slot) {
+                float* dst = st.part + (int64_t)run_start * F * (F + 1);
+                gram_flush<F>(S.u, acc, [&](int a, int cc, float v) { dst[a * (F + 1) + cc] = v; });
+                acc.zero();
+                run_start = c + 1;
+            }
         }
     }
     if constexpr (TC) {
@@ -892,10 +912,13 @@ __global__ void __launch_bounds__(kCtaThreads) k_split_gram(Side side, Params p,
     }
 }
 
-// Sum the chunk Grams of each slot in chunk order, add the regulariser.
+// Sum the partial Grams of each slot in chunk order, add the regulariser.
+// A chunk holds a partial when it starts a run: its index is a multiple of
+// `per` (the contiguous chunk range of a CTA; 1 = every chunk) or it begins
+// its row.
 template <int F>
 __global__ void __launch_bounds__(kCtaThreads) k_split_reduce(Side side, Params p, SplitPlan sp, SplitState st,
-                                                              float* __restrict__ G_aug) {
+                                                              float* __restrict__ G_aug, int per) {
     const int slot = blockIdx.x;
     const int64_t row = sp.row[slot];
     const long long n = side.indptr[row + 1] - side.indptr[row];
@@ -904,7 +927,8 @@ __global__ void __launch_bounds__(kCtaThreads) k_split_reduce(Side side, Params 
     float* dst = G_aug + (int64_t)slot * F * (F + 1);
     for (int e = threadIdx.x; e < F * (F + 1); e += kCtaThreads) {
         float v = 0.f;
-        for (int c = c0; c < c1; ++c) v += st.part[(int64_t)c * F * (F + 1) + e];
+        for (int c = c0; c < c1; c = (c / per + 1) * per)  // the row's first chunk, then range starts
+            v += st.part[(int64_t)c * F * (F + 1) + e];
         const int a = e / (F + 1), b = e % (F + 1);
         if (a == b) v = (a < p.f) ? v + reg : 1.f;
         dst[e] = v;

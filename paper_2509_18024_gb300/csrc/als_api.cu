@@ -524,23 +524,24 @@ int launch_split(als_handle* h, const Plan& pl, const Side& side, const Params& 
     auto gkern = als::k_split_gram<F, ENG>;
     size_t smem = sizeof(als::SplitGramSmem<F, ENG>);
     ALS_CUDA(h, cudaFuncSetAttribute(gkern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int ggrid = pl.n_chunks, per = 1;
+    // Persistent: every resident CTA takes a contiguous range of chunks.
+    int ggrid = pl.n_chunks;
     if constexpr (ENG != als::ENG_CUDA) {
         int rc = tc_launch_shape(h, gkern, smem, ENG, als::TcCfg<F, als::tc_prec(ENG)>::TMEM_COLS, pl.n_chunks, mode,
                                  &smem, &ggrid);
         if (rc) return rc;
     } else {
-        // Persistent: every resident CTA takes a contiguous range of chunks.
         int occ = 0;
         ALS_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gkern, als::kCtaThreads, smem));
         ggrid = std::max(1, std::min(pl.n_chunks, h->n_sm * std::max(occ, 1)));
-        per = (pl.n_chunks + ggrid - 1) / ggrid;
-        ggrid = (pl.n_chunks + per - 1) / per;
     }
+    const int per = (pl.n_chunks + ggrid - 1) / ggrid;
+    ggrid = (pl.n_chunks + per - 1) / per;
     ALS_LAUNCH(h, "split_gram", gkern<<<ggrid, als::kCtaThreads, smem, st>>>(side, p, sp, ss, mode, masks_out, per));
     if (mode != 2)
         ALS_LAUNCH(h, "split_reduce",
-                   als::k_split_reduce<F><<<pl.n_slots, als::kCtaThreads, 0, st>>>(side, p, sp, ss, G_aug, per));
+                   als::k_split_reduce<F><<<pl.n_slots, als::kCtaThreads, 0, st>>>(side, p, sp, ss, G_aug, per,
+                                                                                 als::run_chunks(ENG)));
     return ALS_OK;
 }
 

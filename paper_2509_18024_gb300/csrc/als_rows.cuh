@@ -15,6 +15,11 @@ constexpr int kCtaWarps = kCtaThreads / 32;
 constexpr int kSplitSuper = 4096;  // positions per histogram block of a split row
 constexpr int kGatherBatch = 8;    // independent gathers in flight per thread
 constexpr int kGramBufs = kCtaWarps / 2;  // CUDA-core Gram partial buffers per CTA
+// Longest run of chunks one split-row accumulator sums before its partial is
+// written (keeps the sums blocked for very long rows): 16 chunks for the
+// FP32 register partials, 4 for a TMEM accumulator (the tensor cores' own
+// accumulation order loses more over long runs).
+__host__ __device__ constexpr int run_chunks(int eng) { return eng == 0 ? 16 : 4; }
 
 // Gram engines: FP32 on CUDA cores (n_f <= 32), or tcgen05 in BF16, TF32,
 // or split TF32 (FP32-accurate).
@@ -842,11 +847,14 @@ struct SplitGramSmem {
     uint32_t tmem_slot;
 };
 
-// Masked Gram of split chunks (or masks only when mode == 2). Tensor-core
-// engines: persistent, chunks strided over the CTAs, one partial per chunk in
-// part[c]. CUDA cores: CTA b takes the contiguous chunks [b per, (b+1) per)
-// and keeps its register partials across consecutive chunks of one row; the
-// run's Gram goes to part[first chunk of the run] when the row changes.
+// Masked Gram of split chunks (or masks only when mode == 2). CTA b takes the
+// contiguous chunks [b per, (b+1) per) and keeps one accumulator across
+// consecutive chunks of one row (register partials on CUDA cores, a TMEM
+// accumulator on tensor cores), for at most run_chunks(ENG) chunks; the run's
+// Gram goes to part[first chunk of the run]. A run starts at a range start, a
+// row start, or run_chunks(ENG) chunks after the previous run start. With tensor
+// cores a run's accumulator is read back while the next run's first chunk is
+// staged and its MMAs run.
 template <int F, int ENG>
 __global__ void __launch_bounds__(kCtaThreads) k_split_gram(Side side, Params p, SplitPlan sp, SplitState st,
                                                             int mode, uint32_t* __restrict__ masks_out, int per) {
@@ -862,7 +870,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_split_gram(Side side, Params p,
     if constexpr (TC) {
         if (mode != 2 && blockIdx.x < sp.n_chunks) tc_pipe_setup<F, PREC>(S.tiles, S.bars, &S.tmem_slot, P);
     }
-    int prev_c = -1, prev_acc = 0, prev_len = 0, iter = 0;
+    int prev_c = -1, prev_acc = 0, prev_len = 0, runs = 0;
     auto finish_prev = [&]() {
         if constexpr (TC) {
             if (prev_c < 0) return;
@@ -872,13 +880,12 @@ __global__ void __launch_bounds__(kCtaThreads) k_split_gram(Side side, Params p,
             prev_c = -1;
         }
     };
-    const int c_first = TC ? blockIdx.x : blockIdx.x * per;
-    const int c_end = TC ? sp.n_chunks : min(c_first + per, sp.n_chunks);
-    const int c_step = TC ? gridDim.x : 1;
+    const int c_first = blockIdx.x * per;
+    const int c_end = min(c_first + per, sp.n_chunks);
     GramAcc<F> acc;  // CUDA cores: the current run's warp partials
     if constexpr (!TC) acc.zero();
     int run_start = c_first;
-    for (int c = c_first; c < c_end; c += c_step, ++iter) {
+    for (int c = c_first; c < c_end; ++c) {
         __syncthreads();
         const ChunkInfo ci = chunk_info<F>(sp, side, c);
         stage_tile<F>(S.x, S.r, S.idx, side, p.f, ci.lo + ci.start, ci.len);
@@ -889,14 +896,19 @@ __global__ void __launch_bounds__(kCtaThreads) k_split_gram(Side side, Params p,
                 masks_out[(ci.lo + ci.start) * W + e] = (&S.mask[0][0])[e];
         if (mode == 2) continue;
         if constexpr (TC) {
-            finish_prev();
-            tc_pipe_row<F, PREC, W>(P, S.tiles, S.bars, S.x, S.mask, S.r, ci.len, sym, iter & 1);
-            prev_c = c;
-            prev_acc = iter & 1;
+            const bool fresh = c == c_first || sp.ch_slot[c - 1] != ci.slot || c - run_start == run_chunks(ENG);
+            if (fresh) {
+                finish_prev();  // the previous run (its MMAs overlap this chunk's staging)
+                run_start = c;
+                ++runs;
+            }
+            tc_pipe_row<F, PREC, W>(P, S.tiles, S.bars, S.x, S.mask, S.r, ci.len, sym, runs & 1, fresh);
+            prev_c = run_start;
+            prev_acc = runs & 1;
             prev_len = ci.len;
         } else {
             acc.add_tile(S.x, &S.mask[0][0], S.r, tid >> 5, ci.len, kCtaWarps, sym);
-            if (c + 1 == c_end || sp.ch_slot[c + 1] != ci.slot) {
+            if (c + 1 == c_end || sp.ch_slot[c + 1] != ci.slot || c + 1 - run_start == run_chunks(ENG)) {
                 float* dst = st.part + (int64_t)run_start * F * (F + 1);
                 gram_flush<F>(S.u, acc, [&](int a, int cc, float v) { dst[a * (F + 1) + cc] = v; });
                 acc.zero();
@@ -913,22 +925,35 @@ __global__ void __launch_bounds__(kCtaThreads) k_split_gram(Side side, Params p,
 }
 
 // Sum the partial Grams of each slot in chunk order, add the regulariser.
-// A chunk holds a partial when it starts a run: its index is a multiple of
-// `per` (the contiguous chunk range of a CTA; 1 = every chunk) or it begins
-// its row.
+// A chunk holds a partial when it starts a run (see k_split_gram): the row's
+// first chunk, then from each run start the next multiple of `per` (the
+// chunk range of a CTA) or `run` chunks on, whichever comes first.
 template <int F>
 __global__ void __launch_bounds__(kCtaThreads) k_split_reduce(Side side, Params p, SplitPlan sp, SplitState st,
-                                                              float* __restrict__ G_aug, int per) {
+                                                              float* __restrict__ G_aug, int per, int run) {
     const int slot = blockIdx.x;
     const int64_t row = sp.row[slot];
     const long long n = side.indptr[row + 1] - side.indptr[row];
     const float reg = row_reg(n, p);
     const int c0 = sp.c_begin[slot], c1 = sp.c_begin[slot + 1];
+    const int rb0 = (c0 / per + 1) * per;
     float* dst = G_aug + (int64_t)slot * F * (F + 1);
     for (int e = threadIdx.x; e < F * (F + 1); e += kCtaThreads) {
         float v = 0.f;
-        for (int c = c0; c < c1; c = (c / per + 1) * per)  // the row's first chunk, then range starts
-            v += st.part[(int64_t)c * F * (F + 1) + e];
+        // Run starts: inside each CTA range an arithmetic progression of step
+        // `run` from the row's (or the range's) first chunk; four at a time.
+        const float* pe = st.part + e;
+        constexpr int64_t G = (int64_t)F * (F + 1);
+        for (int c = c0, bound = rb0; c < c1; bound += per) {
+            const int end = min(bound, c1);
+            for (; c + 3 * run < end; c += 4 * run) {
+                const float a0 = pe[c * G], a1 = pe[(c + run) * G], a2 = pe[(c + 2 * run) * G],
+                            a3 = pe[(c + 3 * run) * G];
+                v += ((a0 + a1) + a2) + a3;
+            }
+            for (; c < end; c += run) v += pe[c * G];
+            c = end;
+        }
         const int a = e / (F + 1), b = e % (F + 1);
         if (a == b) v = (a < p.f) ? v + reg : 1.f;
         dst[e] = v;

@@ -174,10 +174,12 @@ __device__ __forceinline__ void tc_pipe_drain(TcPipe& P, uint64_t* bars, int b) 
 }
 
 // Accumulate positions [0, n) of a staged tile into accumulator `acc`
-// (0 or 1), starting it from zero. All threads call it; MMAs stay in flight.
+// (0 or 1), starting it from zero when `fresh` (else adding to what it
+// holds). All threads call it; MMAs stay in flight.
 template <int F, int PREC, int W>
 __device__ __forceinline__ void tc_pipe_row(TcPipe& P, uint8_t* tiles, uint64_t* bars, const float (*x)[xpitch(F)],
-                                            const uint32_t (*mask)[W], const float* r, int n, bool sym, int acc) {
+                                            const uint32_t (*mask)[W], const float* r, int n, bool sym, int acc,
+                                            bool fresh = true) {
     using C = TcCfg<F, PREC>;
     const int tid = threadIdx.x;
     constexpr int KC = C::KC;
@@ -245,7 +247,7 @@ __device__ __forceinline__ void tc_pipe_row(TcPipe& P, uint8_t* tiles, uint64_t*
                     const uint8_t* Bp = (t == 1) ? B1 : B0;
                     const uint64_t ad = umma_desc(smem_addr(Ap) + koff_a, (C::M / 8) * 128, 128);
                     const uint64_t bd = umma_desc(smem_addr(Bp) + koff_b, (C::N / 8) * 128, 128);
-                    const uint32_t accum = (c0 > 0 || ks > 0 || t > 0) ? 1u : 0u;
+                    const uint32_t accum = (!fresh || c0 > 0 || ks > 0 || t > 0) ? 1u : 0u;
                     if (PREC == TC_BF16)
                         asm volatile(
                             "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"

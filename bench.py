@@ -260,7 +260,7 @@ KERNEL_FAMILIES = ("cta_rows", "warp_rows", "solve_rows", "split_init", "split_h
 # dram__bytes_write.sum, averaged over the 6 k_cta_rows launches of a sweep).
 # It holds only for the kernel sources it was taken from: `roofline.traffic`
 # is null once their hash differs.
-TRAFFIC = {"kernel": "cta_rows", "bytes_per_launch": 44.38e6, "sources_sha256_16": "e4a38ce53844a79e"}
+TRAFFIC = {"kernel": "cta_rows", "bytes_per_launch": 44.38e6, "sources_sha256_16": "5b972c38316713a7"}
 
 
 def kernel_sources_hash():

@@ -236,7 +236,7 @@ def gpu_arm(args, p, w, M0, r, rank, world, local_rank):
     top = max(fam, key=lambda k: fam[k][0])
     t_top, n_top = fam[top]
     avg_s = t_top / n_top / 1e3
-    roof = roofline(top, avg_s, p, f, r)
+    roof = roofline(top, avg_s, p, f, r, n_top / args.steps)
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -257,10 +257,11 @@ KERNEL_FAMILIES = ("cta_rows", "warp_rows", "solve_rows", "split_init", "split_h
 
 # DRAM traffic of the dominant kernel family, from the one-pass ncu capture
 # summarised in profiles/cta_rows_zipf100k_traffic.md (dram__bytes_read.sum +
-# dram__bytes_write.sum, averaged over the 6 k_cta_rows launches of a sweep).
-# It holds only for the kernel sources it was taken from: `roofline.traffic`
-# is null once their hash differs.
-TRAFFIC = {"kernel": "cta_rows", "bytes_per_launch": 44.38e6, "sources_sha256_16": "5b972c38316713a7"}
+# dram__bytes_write.sum, summed over the k_cta_rows launches of one sweep;
+# `roofline.traffic` is that sum over the sweep's measured launches). It
+# holds only for the kernel sources it was taken from: `roofline.traffic` is
+# null once their hash differs.
+TRAFFIC = {"kernel": "cta_rows", "bytes_per_sweep": 266.2e6, "sources_sha256_16": "5b972c38316713a7"}
 
 
 def kernel_sources_hash():
@@ -277,12 +278,13 @@ def kernel_sources_hash():
     return h.hexdigest()[:16]
 
 
-def roofline(top, avg_s, p, f, r):
+def roofline(top, avg_s, p, f, r, launches_per_sweep):
     """Roofline entry of the dominant kernel family: algorithmic FP32 flops
     of the rows it handles (2 s_i f^2 for X*^T X plus 2 s_i f for X*^T r, with
-    s_i = floor(n_i r)), per launch (cta_rows: 3 bucket launches per side)."""
+    s_i = floor(n_i r)), per launch: a sweep's flops over its measured
+    launches of the family (cta_rows: one per run of rows with the same
+    resident CTAs per SM, in each of three buckets per side)."""
     flops = 0.0
-    launches_per_sweep = {"cta_rows": 6, "warp_rows": 1, "split_gram": 2}.get(top, 2)
     for csr in (p.train_rows, p.train_cols):
         L = np.diff(csr.indptr)
         if top == "cta_rows":
@@ -302,7 +304,7 @@ def roofline(top, avg_s, p, f, r):
     achieved = per_launch / avg_s / 1e12
     traffic = None
     if top == TRAFFIC["kernel"] and kernel_sources_hash() == TRAFFIC["sources_sha256_16"]:
-        traffic = TRAFFIC["bytes_per_launch"]
+        traffic = TRAFFIC["bytes_per_sweep"] / launches_per_sweep
     return {"bound": "alu", "achieved": achieved, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP32_ALU_PEAK_TFLOPS, "traffic": traffic, "traffic_unit": "bytes per launch",
             "algorithmic_flops_per_launch": per_launch, "kernel": top,

@@ -44,6 +44,7 @@ struct Plan {
     int n_slots = 0, n_chunks = 0, n_super = 0;
     int64_t max_len = 0;
     std::vector<int64_t> host_indptr;  // the indptr the plan was built from
+    std::vector<int32_t> blen;         // lengths of the bucket rows, in list order
     bool stale = false;                // the buffers were refilled: re-check before use
     int32_t* d_lists = nullptr;  // [warp | bucket0 | bucket1 | bucket2 | split rows | c_begin | ch_slot | ch_start
                                  //  | sc_slot | sc_start]
@@ -390,6 +391,8 @@ int build_plan(als_handle* h, const als_csr* R, Plan** out) {
     p.n_super = (int)sc_slot.size();
     p.max_len = max_len;
     p.host_indptr = indptr;
+    for (auto& v : bucket)
+        for (int32_t r : v) p.blen.push_back((int32_t)(indptr[r + 1] - indptr[r]));
     std::vector<int32_t> lists(warp_rows);
     for (auto& v : bucket) lists.insert(lists.end(), v.begin(), v.end());
     lists.insert(lists.end(), split_rows.begin(), split_rows.end());
@@ -429,6 +432,18 @@ int build_plan(als_handle* h, const als_csr* R, Plan** out) {
     return ALS_OK;
 }
 
+// Resident CTAs per SM of a kCtaThreads-thread kernel with `smem` bytes of
+// dynamic shared memory, from shared memory, registers and warps.
+int cta_occupancy(const cudaFuncAttributes& fa, size_t smem) {
+    const size_t per_sm = 233472;  // shared memory of one SM
+    const size_t reserved = 1024;  // per-CTA reservation
+    const int occ_smem = (int)(per_sm / (smem + fa.sharedSizeBytes + reserved));
+    const int warps = als::kCtaThreads / 32;
+    const int regs_per_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
+    const int occ_regs = regs_per_warp > 0 ? 65536 / (regs_per_warp * warps) : 8;
+    return std::max(1, std::min({occ_smem, occ_regs, 64 / warps}));
+}
+
 // Launch shape of a kernel that may hold tensor memory: CUDA-core engines
 // get one CTA per work item; tensor-core engines a persistent grid whose
 // shared-memory request is padded so that the CTAs resident on one SM never
@@ -447,33 +462,47 @@ int tc_launch_shape(als_handle* h, K kernel, size_t smem, int eng, uint32_t tmem
     ALS_CUDA(h, cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem_out));
     ALS_CUDA(h, cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                                      (int)cudaSharedmemCarveoutMaxShared));
-    // Resident CTAs per SM from shared memory, registers and warps.
     cudaFuncAttributes fa;
     ALS_CUDA(h, cudaFuncGetAttributes(&fa, kernel));
-    const int occ_smem = (int)(per_sm / (*smem_out + fa.sharedSizeBytes + reserved));
-    const int warps = als::kCtaThreads / 32;
-    const int regs_per_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
-    const int occ_regs = regs_per_warp > 0 ? 65536 / (regs_per_warp * warps) : 8;
-    const int occ = std::max(1, std::min({occ_smem, occ_regs, 64 / warps, limit}));
+    const int occ = std::min(cta_occupancy(fa, *smem_out), limit);
     *grid_out = std::min(count, h->n_sm * occ);
     return ALS_OK;
 }
 
-template <int F, int NS, int ENG>
-int launch_cta_bucket(als_handle* h, const Side& side, const Params& p, const int32_t* list, int count, int mode,
-                      float* G_aug, uint32_t* masks_out, const uint32_t* tcol) {
+// One bucket of CTA-resident rows. Its rows are sorted by length, longest
+// first (lens: their lengths on the host): one launch per run of rows that
+// reach the same number of resident CTAs per SM, its shared memory sized for
+// the run's longest row.
+template <int F, int ENG>
+int launch_cta_bucket(als_handle* h, const Side& side, const Params& p, const int32_t* list, const int32_t* lens,
+                      int count, int mode, float* G_aug, uint32_t* masks_out, const uint32_t* tcol) {
     if (count == 0) return ALS_OK;
-    auto kern = als::k_cta_rows<F, NS, ENG>;
-    size_t smem = sizeof(als::CtaSmem<F, NS, ENG>);
-    ALS_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int grid = count;
-    if constexpr (ENG != als::ENG_CUDA) {
-        int rc = tc_launch_shape(h, kern, smem, ENG, als::TcCfg<F, als::tc_prec(ENG)>::TMEM_COLS, count, mode, &smem,
-                                 &grid);
-        if (rc) return rc;
+    using L = als::CtaLayout<F, ENG>;
+    auto kern = als::k_cta_rows<F, ENG>;
+    cudaFuncAttributes fa;
+    ALS_CUDA(h, cudaFuncGetAttributes(&fa, kern));
+    // Tensor-core engines hold TMEM: at most 512 / (2 accumulators) columns' worth of CTAs per SM.
+    const int limit =
+        ENG == als::ENG_CUDA ? 64 : std::max(1, (int)(512 / (2 * als::TcCfg<F, als::tc_prec(ENG)>::TMEM_COLS)));
+    auto occ_of = [&](int len) { return std::min(cta_occupancy(fa, L::bytes(std::max(len, 1))), limit); };
+    for (int a = 0; a < count;) {
+        const int cap = std::max(lens[a], 1);
+        const int occ = occ_of(cap);
+        const int b = (int)(std::partition_point(lens + a, lens + count, [&](int32_t len) { return occ_of(len) == occ; }) -
+                            lens);
+        size_t smem = L::bytes(cap);
+        ALS_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int grid = b - a;
+        if constexpr (ENG != als::ENG_CUDA) {
+            int rc = tc_launch_shape(h, kern, smem, ENG, als::TcCfg<F, als::tc_prec(ENG)>::TMEM_COLS, b - a, mode,
+                                     &smem, &grid);
+            if (rc) return rc;
+        }
+        ALS_LAUNCH(h, "cta_rows", kern<<<grid, als::kCtaThreads, smem, h->stream>>>(
+                                      side, p, list + a, b - a, cap, mode, G_aug + (size_t)a * F * (F + 1),
+                                      masks_out, tcol));
+        a = b;
     }
-    ALS_LAUNCH(h, "cta_rows", kern<<<grid, als::kCtaThreads, smem, h->stream>>>(side, p, list, count, mode, G_aug,
-                                                                              masks_out, tcol));
     return ALS_OK;
 }
 
@@ -582,14 +611,6 @@ int launch_fp64(als_handle* h, const Side& side, const Params& p, const uint32_t
     return ALS_OK;
 }
 
-// Bucket capacities as template arguments.
-template <int F>
-struct Caps {
-    static constexpr int c0 = F <= 32 ? 128 : (F == 64 ? 128 : 32);
-    static constexpr int c1 = F <= 32 ? 512 : (F == 64 ? 256 : 64);
-    static constexpr int c2 = F <= 32 ? 1024 : (F == 64 ? 512 : 128);
-};
-
 // mode 0: solve into X_out; 1: assembled systems into G_out/b_out; 2: masks only.
 template <int F, int ENG>
 int run_side(als_handle* h, const Plan& pl, const Side& side, int mode, float* X_out, int32_t* flags_out,
@@ -636,15 +657,12 @@ int run_side(als_handle* h, const Plan& pl, const Side& side, int mode, float* X
         const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)h->n_sm * 4));
         ALS_LAUNCH(h, "colmax", als::k_colmax<F><<<blocks, 256, 0, st>>>(side.Y, side.n_cols, p.f, tcol));
     }
-    rc = launch_cta_bucket<F, Caps<F>::c2, ENG>(h, side, p, lists + pl.off_bucket(2), pl.n_bucket[2], mode, aug_b2,
-                                               masks_out, tcol);
-    if (rc) return rc;
-    rc = launch_cta_bucket<F, Caps<F>::c1, ENG>(h, side, p, lists + pl.off_bucket(1), pl.n_bucket[1], mode, aug_b1,
-                                               masks_out, tcol);
-    if (rc) return rc;
-    rc = launch_cta_bucket<F, Caps<F>::c0, ENG>(h, side, p, lists + pl.off_bucket(0), pl.n_bucket[0], mode, aug_b0,
-                                               masks_out, tcol);
-    if (rc) return rc;
+    for (int b = 2; b >= 0; --b) {
+        float* aug = b == 2 ? aug_b2 : (b == 1 ? aug_b1 : aug_b0);
+        rc = launch_cta_bucket<F, ENG>(h, side, p, lists + pl.off_bucket(b), pl.blen.data() + (pl.off_bucket(b) - pl.n_warp),
+                                       pl.n_bucket[b], mode, aug, masks_out, tcol);
+        if (rc) return rc;
+    }
     if constexpr (F <= 32) {
         if (n_warp > 0)
             ALS_LAUNCH(h, "warp_rows", als::k_warp_rows<F><<<(n_warp + 7) / 8, 256, 0, st>>>(

@@ -256,21 +256,6 @@ __device__ __forceinline__ void gram_flush(uint8_t* scratch, const GramAcc<F>& g
     }
 }
 
-// Masked Gram of positions [0, cn) of a staged tile on CUDA cores (FP32,
-// n_f <= 32). The result (no regulariser) goes to out(a, c, v) for a < F,
-// c <= F, called once per value by some thread. scratch: per-warp partials.
-template <int F, int ENG, class Out>
-__device__ __forceinline__ void gram_tile(uint8_t* scratch, uint64_t*, uint32_t*, const float (*x)[xpitch(F)],
-                                          const uint32_t (*mask)[MaskWords<F>::value], const float* r, int cn,
-                                          bool sym, Out out) {
-    static_assert(ENG == ENG_CUDA && F <= 32, "CUDA-core Gram is built for n_f <= 32");
-    const int tid = threadIdx.x, warp = tid >> 5;
-    GramAcc<F> g;
-    g.zero();
-    g.add_tile(x, &mask[0][0], r, warp, cn, kCtaWarps, sym);
-    gram_flush<F>(scratch, g, out);
-}
-
 // ---------------------------------------------------------------------------
 // Largest exponent of |y_a| over every row of the factor Y (n_cols x f), per
 // column: tcol[a] (zeroed before the launch). The CES window of a row starts
@@ -491,46 +476,66 @@ __device__ __forceinline__ void quad_select(const float (*x)[xpitch(F)], int n, 
 }
 
 // ---------------------------------------------------------------------------
-// CTA per row, slice resident in shared memory (n_i <= NS).
+// CTA per row, slice resident in shared memory.
 // Bytes of the two tensor-core tile buffers of an engine (16 for CUDA cores).
 template <int F, int ENG>
 struct TileBytes {
     static constexpr int value = ENG == ENG_CUDA ? 16 : 2 * TcCfg<F, tc_prec(ENG)>::TILE_BYTES;
 };
 
-template <int F, int NS, int ENG>
-struct CtaSmem {
+// Shared memory of k_cta_rows, in bytes from the (1024-byte aligned) base:
+// a fixed part - tensor-core tiles, per-warp selection bins, barriers, the
+// keep rules of the F columns - then the staged slice [x | r | idx | mask],
+// sized for the launch's capacity (its longest row). The CUDA-core Gram's
+// per-warp partials reuse the x area once the tile has been consumed.
+template <int F, int ENG>
+struct CtaLayout {
     static constexpr int W = MaskWords<F>::value;
-    static constexpr int HIST_BYTES = kCtaWarps * kQuadHistWords * 4;
-    static constexpr int GRAM_BYTES = ENG == ENG_CUDA ? kGramBufs * F * (F + 1) * 4 : 0;
-    static constexpr int U_BYTES = HIST_BYTES > GRAM_BYTES ? HIST_BYTES : GRAM_BYTES;
-    float x[NS][xpitch(F)];
-    float r[NS];
-    int32_t idx[NS];
-    uint32_t mask[NS][W];
-    __align__(1024) uint8_t u[U_BYTES];  // per-warp selection bins (then CUDA-core Gram partials)
-    __align__(1024) uint8_t tiles[TileBytes<F, ENG>::value];  // tensor-core operands
-    uint64_t bars[2];
-    uint32_t tmem_slot;
-    uint32_t P[F];
-    uint32_t Mk[F];
-    int32_t cut[F];
+    static constexpr size_t HIST_BYTES = (size_t)kCtaWarps * kQuadHistWords * 4;
+    static constexpr size_t GRAM_BYTES = ENG == ENG_CUDA ? (size_t)kGramBufs * F * (F + 1) * 4 : 0;
+    static constexpr size_t up16(size_t b) { return (b + 15) / 16 * 16; }
+    static constexpr size_t tiles = 0;
+    static constexpr size_t u = up16(TileBytes<F, ENG>::value);
+    static constexpr size_t bars = u + HIST_BYTES;
+    static constexpr size_t tmem_slot = bars + 2 * sizeof(uint64_t);
+    static constexpr size_t P = tmem_slot + 16;
+    static constexpr size_t Mk = P + (size_t)F * 4;
+    static constexpr size_t cut = Mk + (size_t)F * 4;
+    static constexpr size_t x = up16(cut + (size_t)F * 4);
+    __host__ __device__ static constexpr size_t x_bytes(int cap) {
+        return (size_t)cap * xpitch(F) * 4 > GRAM_BYTES ? (size_t)cap * xpitch(F) * 4 : GRAM_BYTES;
+    }
+    __host__ __device__ static constexpr size_t r(int cap) { return x + x_bytes(cap); }
+    __host__ __device__ static constexpr size_t idx(int cap) { return r(cap) + (size_t)cap * 4; }
+    __host__ __device__ static constexpr size_t mask(int cap) { return idx(cap) + (size_t)cap * 4; }
+    __host__ __device__ static constexpr size_t bytes(int cap) { return up16(mask(cap) + (size_t)cap * W * 4); }
 };
 
 // mode 0/1: write the augmented system of list entry w to G_aug[w]; mode 2:
-// masks only. CTAs loop over list entries w = blockIdx.x + k gridDim.x; with
-// a tensor-core engine the grid is persistent, TMEM and tiles are set up
-// once per CTA, and each row's accumulator is read back after the next row
-// has been staged and selected (its MMAs run meanwhile).
-template <int F, int NS, int ENG>
+// masks only. Every listed row has at most `cap` positions (the capacity the
+// shared memory was sized for). CTAs loop over list entries w = blockIdx.x +
+// k gridDim.x; with a tensor-core engine the grid is persistent, TMEM and
+// tiles are set up once per CTA, and each row's accumulator is read back
+// after the next row has been staged and selected (its MMAs run meanwhile).
+template <int F, int ENG>
 __global__ void __launch_bounds__(kCtaThreads, ENG == ENG_CUDA ? 4 : 1) k_cta_rows(Side side, Params p, const int32_t* __restrict__ rows,
-                                                          int n_list, int mode, float* __restrict__ G_aug,
+                                                          int n_list, int cap, int mode, float* __restrict__ G_aug,
                                                           uint32_t* __restrict__ masks_out,
                                                           const uint32_t* __restrict__ tcol) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    using Smem = CtaSmem<F, NS, ENG>;
-    Smem& S = *reinterpret_cast<Smem*>(smem_raw);
-    constexpr int W = Smem::W;
+    using L = CtaLayout<F, ENG>;
+    constexpr int W = L::W;
+    uint8_t* const s_tiles = smem_raw + L::tiles;
+    uint8_t* const s_u = smem_raw + L::u;
+    uint64_t* const s_bars = reinterpret_cast<uint64_t*>(smem_raw + L::bars);
+    uint32_t* const s_tmem = reinterpret_cast<uint32_t*>(smem_raw + L::tmem_slot);
+    uint32_t* const s_P = reinterpret_cast<uint32_t*>(smem_raw + L::P);
+    uint32_t* const s_Mk = reinterpret_cast<uint32_t*>(smem_raw + L::Mk);
+    int32_t* const s_cut = reinterpret_cast<int32_t*>(smem_raw + L::cut);
+    float (*const s_x)[xpitch(F)] = reinterpret_cast<float (*)[xpitch(F)]>(smem_raw + L::x);
+    float* const s_r = reinterpret_cast<float*>(smem_raw + L::r(cap));
+    int32_t* const s_idx = reinterpret_cast<int32_t*>(smem_raw + L::idx(cap));
+    uint32_t (*const s_mask)[W] = reinterpret_cast<uint32_t (*)[W]>(smem_raw + L::mask(cap));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int f = p.f;
     constexpr bool TC = ENG != ENG_CUDA;
@@ -538,15 +543,19 @@ __global__ void __launch_bounds__(kCtaThreads, ENG == ENG_CUDA ? 4 : 1) k_cta_ro
     const bool sym = p.gram_mode == GRAM_SYM;
     TcPipe P;
     if constexpr (TC) {
-        if (mode != 2 && blockIdx.x < n_list) tc_pipe_setup<F, PREC>(S.tiles, S.bars, &S.tmem_slot, P);
+        if (mode != 2 && blockIdx.x < n_list) tc_pipe_setup<F, PREC>(s_tiles, s_bars, s_tmem, P);
     }
+    // This warp's selection bins: zeroed once, every selection leaves them zero.
+    uint32_t* const H = reinterpret_cast<uint32_t*>(s_u) + warp * kQuadHistWords;
+    for (int e = lane; e < kQuadHistWords / 4; e += 32) reinterpret_cast<uint4*>(H)[e] = make_uint4(0u, 0u, 0u, 0u);
+    __syncwarp();
     int prev_w = -1, prev_n = 0, prev_acc = 0, iter = 0;
     auto finish_prev = [&]() {
         if constexpr (TC) {
             if (prev_w < 0) return;
             float* dst = G_aug + (int64_t)prev_w * F * (F + 1);
             const float reg = row_reg(prev_n, p);
-            tc_pipe_finish<F, PREC>(P, S.bars, prev_acc, prev_n == 0, [&](int a, int c, float v) {
+            tc_pipe_finish<F, PREC>(P, s_bars, prev_acc, prev_n == 0, [&](int a, int c, float v) {
                 if (a == c) v = (a < f) ? v + reg : 1.f;
                 dst[a * (F + 1) + c] = v;
             });
@@ -559,31 +568,29 @@ __global__ void __launch_bounds__(kCtaThreads, ENG == ENG_CUDA ? 4 : 1) k_cta_ro
     const int64_t lo = side.indptr[i];
     const int n = (int)(side.indptr[i + 1] - lo);
     const long long s = row_budget(n, p);
-    stage_tile<F>(S.x, S.r, S.idx, side, f, lo, n);
-    // CES: warp w selects the column quads w, w + 8, ... on its own bins
-    // (cleared first: the CUDA-core Gram of the previous row reused them).
-    {
-        uint32_t* H = reinterpret_cast<uint32_t*>(S.u) + warp * kQuadHistWords;
-        for (int e = lane; e < kQuadHistWords / 4; e += 32) reinterpret_cast<uint4*>(H)[e] = make_uint4(0u, 0u, 0u, 0u);
-        __syncwarp();
-        for (int q = warp; q < F / 4; q += kCtaWarps) quad_select<F>(S.x, n, f, s, q, H, tcol, S.P, S.Mk, S.cut);
-    }
+    stage_tile<F>(s_x, s_r, s_idx, side, f, lo, n);
+    // CES: warp w selects the column quads w, w + 8, ... on its own bins.
+    for (int q = warp; q < F / 4; q += kCtaWarps) quad_select<F>(s_x, n, f, s, q, H, tcol, s_P, s_Mk, s_cut);
     __syncthreads();
-    build_masks<F>(S.mask, S.x, n, 0, S.P, S.Mk, S.cut);
+    build_masks<F>(s_mask, s_x, n, 0, s_P, s_Mk, s_cut);
     __syncthreads();
     if (masks_out != nullptr)
-        for (int e = tid; e < n * W; e += kCtaThreads) masks_out[lo * W + e] = (&S.mask[0][0])[e];
+        for (int e = tid; e < n * W; e += kCtaThreads) masks_out[lo * W + e] = (&s_mask[0][0])[e];
     if (mode == 2) continue;
     if constexpr (TC) {
         finish_prev();
-        tc_pipe_row<F, PREC, W>(P, S.tiles, S.bars, S.x, S.mask, S.r, n, sym, iter & 1);
+        tc_pipe_row<F, PREC, W>(P, s_tiles, s_bars, s_x, s_mask, s_r, n, sym, iter & 1);
         prev_w = w;
         prev_n = n;
         prev_acc = iter & 1;
     } else {
         float* dst = G_aug + (int64_t)w * F * (F + 1);
         const float reg = row_reg(n, p);
-        gram_tile<F, ENG>(S.u, nullptr, nullptr, S.x, S.mask, S.r, n, sym, [&](int a, int c, float v) {
+        GramAcc<F> g;
+        g.zero();
+        g.add_tile(s_x, &s_mask[0][0], s_r, warp, n, kCtaWarps, sym);
+        __syncthreads();  // the partials overwrite the x area
+        gram_flush<F>(smem_raw + L::x, g, [&](int a, int c, float v) {
             if (a == c) v = (a < f) ? v + reg : 1.f;
             dst[a * (F + 1) + c] = v;
         });

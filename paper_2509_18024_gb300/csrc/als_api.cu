@@ -96,6 +96,10 @@ struct DevBuf {
 struct als_handle {
     als_options opt;
     cudaStream_t stream = nullptr;
+    // Second stream of a half-sweep (the split-row chain runs on it, beside
+    // the resident rows) and its fork/join events; made on first use.
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int device = 0;
     std::vector<Plan> plans;
     als_tuning tuning{0, 1, 0, 0.0};
@@ -444,6 +448,17 @@ int cta_occupancy(const cudaFuncAttributes& fa, size_t smem) {
     return std::max(1, std::min({occ_smem, occ_regs, 64 / warps}));
 }
 
+// The handle's second stream (highest priority) and fork/join events.
+int ensure_aux(als_handle* h) {
+    if (h->aux) return ALS_OK;
+    int least = 0, greatest = 0;
+    ALS_CUDA(h, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    ALS_CUDA(h, cudaStreamCreateWithPriority(&h->aux, cudaStreamNonBlocking, greatest));
+    ALS_CUDA(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    ALS_CUDA(h, cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    return ALS_OK;
+}
+
 // Launch shape of a kernel that may hold tensor memory: CUDA-core engines
 // get one CTA per work item; tensor-core engines a persistent grid whose
 // shared-memory request is padded so that the CTAs resident on one SM never
@@ -646,8 +661,25 @@ int run_side(als_handle* h, const Plan& pl, const Side& side, int mode, float* X
     float* aug_b1 = aug_b0 + (size_t)pl.n_bucket[0] * FF;
     float* aug_b2 = aug_b1 + (size_t)pl.n_bucket[1] * FF;
     float* aug_split = aug_b2 + (size_t)pl.n_bucket[2] * FF;
-    rc = launch_split<F, ENG>(h, pl, side, p, mode, aug_split, masks_out);
-    if (rc) return rc;
+    // The split-row chain and the resident rows write disjoint systems and
+    // masks: the chain forks onto the second stream (higher priority: it is
+    // the longer dependent sequence) and joins before the solve. Profiling
+    // keeps one stream, so that each launch's events time it alone.
+    const bool overlap = pl.n_slots > 0 && pl.n_cta_like() + n_warp > pl.n_slots && !h->profiling;
+    if (overlap) {
+        rc = ensure_aux(h);
+        if (rc) return rc;
+        ALS_CUDA(h, cudaEventRecord(h->ev_fork, st));
+        ALS_CUDA(h, cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+        h->stream = h->aux;
+        rc = launch_split<F, ENG>(h, pl, side, p, mode, aug_split, masks_out);
+        h->stream = st;
+        if (rc) return rc;
+        ALS_CUDA(h, cudaEventRecord(h->ev_join, h->aux));
+    } else {
+        rc = launch_split<F, ENG>(h, pl, side, p, mode, aug_split, masks_out);
+        if (rc) return rc;
+    }
     const int32_t* lists = pl.d_lists;
     // Largest exponent per factor column: the top of the resident rows' CES window.
     uint32_t* tcol = reinterpret_cast<uint32_t*>(static_cast<char*>(h->misc.p) + kColmaxOffset);
@@ -668,6 +700,7 @@ int run_side(als_handle* h, const Plan& pl, const Side& side, int mode, float* X
             ALS_LAUNCH(h, "warp_rows", als::k_warp_rows<F><<<(n_warp + 7) / 8, 256, 0, st>>>(
                                            side, p, lists, n_warp, mode == 2, masks_out, aug_warp));
     }
+    if (overlap) ALS_CUDA(h, cudaStreamWaitEvent(st, h->ev_join, 0));
     // Wide systems keep their LU factors (in G_aug) and permutations when a
     // refinement follows: its corrections then need substitutions only.
     int32_t* perm_buf = nullptr;
@@ -849,6 +882,9 @@ int als_destroy(als_handle* h) {
     }
     for (auto e : h->event_pool) cudaEventDestroy(e);
     if (h->fit_graph.exec) cudaGraphExecDestroy(h->fit_graph.exec);
+    if (h->aux) cudaStreamDestroy(h->aux);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     for (DevBuf* b : {&h->g_aug, &h->misc, &h->host_in, &h->masks, &h->fb_list, &h->delta, &h->perms})
         if (b->p) cudaFree(b->p);
     delete h;

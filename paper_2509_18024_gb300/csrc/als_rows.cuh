@@ -498,7 +498,8 @@ struct CtaLayout {
     static constexpr size_t u = up16(TileBytes<F, ENG>::value);
     static constexpr size_t bars = u + HIST_BYTES;
     static constexpr size_t tmem_slot = bars + 2 * sizeof(uint64_t);
-    static constexpr size_t P = tmem_slot + 16;
+    static constexpr size_t row = tmem_slot + 16;  // the row's budget s_i (8 bytes) and regulariser (4)
+    static constexpr size_t P = row + 16;
     static constexpr size_t Mk = P + (size_t)F * 4;
     static constexpr size_t cut = Mk + (size_t)F * 4;
     static constexpr size_t x = up16(cut + (size_t)F * 4);
@@ -529,6 +530,8 @@ __global__ void __launch_bounds__(kCtaThreads, ENG == ENG_CUDA ? 4 : 1) k_cta_ro
     uint8_t* const s_u = smem_raw + L::u;
     uint64_t* const s_bars = reinterpret_cast<uint64_t*>(smem_raw + L::bars);
     uint32_t* const s_tmem = reinterpret_cast<uint32_t*>(smem_raw + L::tmem_slot);
+    long long* const s_budget = reinterpret_cast<long long*>(smem_raw + L::row);
+    float* const s_reg = reinterpret_cast<float*>(smem_raw + L::row + 8);
     uint32_t* const s_P = reinterpret_cast<uint32_t*>(smem_raw + L::P);
     uint32_t* const s_Mk = reinterpret_cast<uint32_t*>(smem_raw + L::Mk);
     int32_t* const s_cut = reinterpret_cast<int32_t*>(smem_raw + L::cut);
@@ -550,11 +553,12 @@ __global__ void __launch_bounds__(kCtaThreads, ENG == ENG_CUDA ? 4 : 1) k_cta_ro
     for (int e = lane; e < kQuadHistWords / 4; e += 32) reinterpret_cast<uint4*>(H)[e] = make_uint4(0u, 0u, 0u, 0u);
     __syncwarp();
     int prev_w = -1, prev_n = 0, prev_acc = 0, iter = 0;
+    float prev_reg = 0.f;
     auto finish_prev = [&]() {
         if constexpr (TC) {
             if (prev_w < 0) return;
             float* dst = G_aug + (int64_t)prev_w * F * (F + 1);
-            const float reg = row_reg(prev_n, p);
+            const float reg = prev_reg;
             tc_pipe_finish<F, PREC>(P, s_bars, prev_acc, prev_n == 0, [&](int a, int c, float v) {
                 if (a == c) v = (a < f) ? v + reg : 1.f;
                 dst[a * (F + 1) + c] = v;
@@ -567,8 +571,15 @@ __global__ void __launch_bounds__(kCtaThreads, ENG == ENG_CUDA ? 4 : 1) k_cta_ro
     const int64_t i = rows[w];
     const int64_t lo = side.indptr[i];
     const int n = (int)(side.indptr[i + 1] - lo);
-    const long long s = row_budget(n, p);
+    // The budget and regulariser take FP64 steps (a slow pipe here): one
+    // thread evaluates them; stage_tile's barrier publishes them.
+    if (tid == 0) {
+        *s_budget = row_budget(n, p);
+        *s_reg = row_reg(n, p);
+    }
     stage_tile<F>(s_x, s_r, s_idx, side, f, lo, n);
+    const long long s = *s_budget;
+    const float reg = *s_reg;
     // CES: warp w selects the column quads w, w + 8, ... on its own bins.
     for (int q = warp; q < F / 4; q += kCtaWarps) quad_select<F>(s_x, n, f, s, q, H, tcol, s_P, s_Mk, s_cut);
     __syncthreads();
@@ -582,10 +593,10 @@ __global__ void __launch_bounds__(kCtaThreads, ENG == ENG_CUDA ? 4 : 1) k_cta_ro
         tc_pipe_row<F, PREC, W>(P, s_tiles, s_bars, s_x, s_mask, s_r, n, sym, iter & 1);
         prev_w = w;
         prev_n = n;
+        prev_reg = reg;
         prev_acc = iter & 1;
     } else {
         float* dst = G_aug + (int64_t)w * F * (F + 1);
-        const float reg = row_reg(n, p);
         GramAcc<F> g;
         g.zero();
         g.add_tile(s_x, &s_mask[0][0], s_r, warp, n, kCtaWarps, sym);

@@ -196,6 +196,34 @@ def test_solve_flags_singular_and_ratio(core):
     assert flags[1] == 1 and flags[2] == 0
 
 
+@pytest.mark.parametrize("mode", ["asym", "sym"])
+def test_solve_padded_odd_count_with_bad_systems(core, mode):
+    # n_f = 30 pads to 32 (two identity rows per system); an odd count of
+    # systems, with singular (all-zero) systems at an even and at the last
+    # position and a near-singular one at an odd position.
+    rng = np.random.default_rng(9)
+    n, f = 9, 30
+    A = rng.standard_normal((n, f, f))
+    if mode == "sym":
+        A = A @ np.transpose(A, (0, 2, 1)) + f * np.eye(f)
+    else:
+        A = A + 6 * np.eye(f)
+    A[2] = 0.0                                   # singular
+    A[5] = np.diag(np.r_[np.ones(f - 1), 1e-8])  # pivot ratio 1e8
+    A[8] = 0.0                                   # singular, last
+    A = A.astype(np.float32)
+    b = rng.standard_normal((n, f)).astype(np.float32)
+    eng = core.CoreALS(f, 0.05, 0.25, gram_mode=mode)
+    X, flags = eng.solve(torch.as_tensor(A).cuda(), torch.as_tensor(b).cuda())
+    Xo, fo, _ = oracle.solve_batch(A.astype(np.float64), b.astype(np.float64), 0 if mode == "asym" else 1)
+    flags, X = flags.cpu().numpy(), X.cpu().numpy()
+    assert np.array_equal(flags, fo), (flags, fo)
+    assert flags[2] & 2 and flags[8] & 2 and flags[5] == 1
+    assert np.all(X[2] == 0) and np.all(X[8] == 0)
+    ok = [i for i in range(n) if fo[i] == 0]
+    assert rel_fro(X[ok], Xo[ok]) <= 1e-4
+
+
 # -------------------------------------------------------- full runs / e2e
 def test_fit_small_rmse_matches_oracle(core, small):
     M0 = synth.init_factor(small.n_m, small.f, 1000)
@@ -232,6 +260,26 @@ def test_deterministic(core, small):
     a = eng.half_sweep(Ru, M0).cpu().numpy()
     b = eng.half_sweep(Ru, M0).cpu().numpy()
     assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("f,prec", [(32, 0), (64, 0), (128, 2)])
+def test_split_chain_on_second_stream_is_bit_identical(core, f, prec):
+    # Without per-launch profiling the split-row chain runs on the handle's
+    # second stream beside the resident rows; with it, everything runs on one
+    # stream in order. Both write disjoint rows: the results must agree bit
+    # for bit (n_f = 32 on CUDA cores; 64 and 128 on the tensor cores).
+    csr, Y = rows_problem(LENGTHS + [5000], 6000, f, seed=31)
+    eng = core.CoreALS(f, 0.05, 0.25, precision=prec)
+    R = core.DeviceCSR.from_host(csr)
+    Yd = torch.as_tensor(Y).cuda()
+    flags_a = torch.zeros(csr.n_rows, dtype=torch.int32, device="cuda")
+    flags_b = torch.zeros(csr.n_rows, dtype=torch.int32, device="cuda")
+    Xa = eng.half_sweep(R, Yd, flags=flags_a).cpu().numpy()
+    eng.profile(True)
+    Xb = eng.half_sweep(R, Yd, flags=flags_b).cpu().numpy()
+    eng.profile(False)
+    assert np.array_equal(Xa, Xb)
+    assert np.array_equal(flags_a.cpu().numpy(), flags_b.cpu().numpy())
 
 
 # ------------------------------------------------------------ bad inputs

@@ -96,10 +96,12 @@ struct DevBuf {
 struct als_handle {
     als_options opt;
     cudaStream_t stream = nullptr;
-    // Second stream of a half-sweep (the split-row chain runs on it, beside
-    // the resident rows) and its fork/join events; made on first use.
-    cudaStream_t aux = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // Side streams of a half-sweep (the split-row chain on aux, the warp
+    // rows on aux2, the solves of the CTA-resident rows' buckets on aux3,
+    // beside their assembly) and their fork/join events; made on first use.
+    cudaStream_t aux = nullptr, aux2 = nullptr, aux3 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr, ev_join3 = nullptr;
+    cudaEvent_t ev_bucket[3] = {nullptr, nullptr, nullptr};
     int device = 0;
     std::vector<Plan> plans;
     als_tuning tuning{0, 1, 0, 0.0};
@@ -448,14 +450,17 @@ int cta_occupancy(const cudaFuncAttributes& fa, size_t smem) {
     return std::max(1, std::min({occ_smem, occ_regs, 64 / warps}));
 }
 
-// The handle's second stream (highest priority) and fork/join events.
+// The handle's side streams (aux at the highest priority) and fork/join events.
 int ensure_aux(als_handle* h) {
-    if (h->aux) return ALS_OK;
+    if (h->ev_bucket[2]) return ALS_OK;
     int least = 0, greatest = 0;
     ALS_CUDA(h, cudaDeviceGetStreamPriorityRange(&least, &greatest));
-    ALS_CUDA(h, cudaStreamCreateWithPriority(&h->aux, cudaStreamNonBlocking, greatest));
-    ALS_CUDA(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
-    ALS_CUDA(h, cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    if (!h->aux) ALS_CUDA(h, cudaStreamCreateWithPriority(&h->aux, cudaStreamNonBlocking, greatest));
+    if (!h->aux2) ALS_CUDA(h, cudaStreamCreateWithPriority(&h->aux2, cudaStreamNonBlocking, least));
+    if (!h->aux3) ALS_CUDA(h, cudaStreamCreateWithPriority(&h->aux3, cudaStreamNonBlocking, least));
+    for (cudaEvent_t* e : {&h->ev_fork, &h->ev_join, &h->ev_join2, &h->ev_join3, &h->ev_bucket[0], &h->ev_bucket[1],
+                           &h->ev_bucket[2]})
+        if (!*e) ALS_CUDA(h, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     return ALS_OK;
 }
 
@@ -589,6 +594,15 @@ int launch_split(als_handle* h, const Plan& pl, const Side& side, const Params& 
     return ALS_OK;
 }
 
+// Warp-per-row CES and Gram of the rows with at most 32 positions (n_f <= 32).
+template <int F>
+int launch_warp_rows(als_handle* h, const Side& side, const Params& p, const int32_t* list, int count, int mode,
+                     uint32_t* masks_out, float* aug) {
+    ALS_LAUNCH(h, "warp_rows", als::k_warp_rows<F><<<(count + 7) / 8, 256, 0, h->stream>>>(
+                                   side, p, list, count, mode == 2, masks_out, aug));
+    return ALS_OK;
+}
+
 // Batched solve of augmented systems listed by `list` (null: identity).
 template <int F>
 int launch_solve(als_handle* h, float* aug, const int32_t* list, int count, const Params& p, float* X_out,
@@ -654,53 +668,16 @@ int run_side(als_handle* h, const Plan& pl, const Side& side, int mode, float* X
         }
     }
     // Augmented systems in row-list order: [warp rows | bucket0 | bucket1 |
-    // bucket2 | split slots], so that one batched solve covers all rows.
+    // bucket2 | split slots].
     constexpr size_t FF = (size_t)F * (F + 1);
+    const int nb = pl.n_bucket[0] + pl.n_bucket[1] + pl.n_bucket[2];
+    const int off_split = n_warp + nb;
     float* aug_warp = G_aug;
     float* aug_b0 = aug_warp + (size_t)n_warp * FF;
     float* aug_b1 = aug_b0 + (size_t)pl.n_bucket[0] * FF;
     float* aug_b2 = aug_b1 + (size_t)pl.n_bucket[1] * FF;
     float* aug_split = aug_b2 + (size_t)pl.n_bucket[2] * FF;
-    // The split-row chain and the resident rows write disjoint systems and
-    // masks: the chain forks onto the second stream (higher priority: it is
-    // the longer dependent sequence) and joins before the solve. Profiling
-    // keeps one stream, so that each launch's events time it alone.
-    const bool overlap = pl.n_slots > 0 && pl.n_cta_like() + n_warp > pl.n_slots && !h->profiling;
-    if (overlap) {
-        rc = ensure_aux(h);
-        if (rc) return rc;
-        ALS_CUDA(h, cudaEventRecord(h->ev_fork, st));
-        ALS_CUDA(h, cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
-        h->stream = h->aux;
-        rc = launch_split<F, ENG>(h, pl, side, p, mode, aug_split, masks_out);
-        h->stream = st;
-        if (rc) return rc;
-        ALS_CUDA(h, cudaEventRecord(h->ev_join, h->aux));
-    } else {
-        rc = launch_split<F, ENG>(h, pl, side, p, mode, aug_split, masks_out);
-        if (rc) return rc;
-    }
     const int32_t* lists = pl.d_lists;
-    // Largest exponent per factor column: the top of the resident rows' CES window.
-    uint32_t* tcol = reinterpret_cast<uint32_t*>(static_cast<char*>(h->misc.p) + kColmaxOffset);
-    if (pl.n_bucket[0] + pl.n_bucket[1] + pl.n_bucket[2] > 0) {
-        ALS_CUDA(h, cudaMemsetAsync(tcol, 0, (size_t)F * sizeof(uint32_t), st));
-        const int64_t total = side.n_cols * (int64_t)p.f;
-        const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)h->n_sm * 4));
-        ALS_LAUNCH(h, "colmax", als::k_colmax<F><<<blocks, 256, 0, st>>>(side.Y, side.n_cols, p.f, tcol));
-    }
-    for (int b = 2; b >= 0; --b) {
-        float* aug = b == 2 ? aug_b2 : (b == 1 ? aug_b1 : aug_b0);
-        rc = launch_cta_bucket<F, ENG>(h, side, p, lists + pl.off_bucket(b), pl.blen.data() + (pl.off_bucket(b) - pl.n_warp),
-                                       pl.n_bucket[b], mode, aug, masks_out, tcol);
-        if (rc) return rc;
-    }
-    if constexpr (F <= 32) {
-        if (n_warp > 0)
-            ALS_LAUNCH(h, "warp_rows", als::k_warp_rows<F><<<(n_warp + 7) / 8, 256, 0, st>>>(
-                                           side, p, lists, n_warp, mode == 2, masks_out, aug_warp));
-    }
-    if (overlap) ALS_CUDA(h, cudaStreamWaitEvent(st, h->ev_join, 0));
     // Wide systems keep their LU factors (in G_aug) and permutations when a
     // refinement follows: its corrections then need substitutions only.
     int32_t* perm_buf = nullptr;
@@ -709,12 +686,87 @@ int run_side(als_handle* h, const Plan& pl, const Side& side, int mode, float* X
         if (rc) return rc;
         perm_buf = reinterpret_cast<int32_t*>(h->perms.p);
     }
-    if (mode == 0) {
-        rc = launch_solve<F>(h, G_aug, lists, n_aug, p, X_out, flags_out, fb, nullptr, perm_buf);
+    // Solve of the list entries [off, off + cnt) (mode 0).
+    auto solve_range = [&](int off, int cnt) -> int {
+        if (mode != 0 || cnt == 0) return ALS_OK;
+        return launch_solve<F>(h, G_aug + (size_t)off * FF, lists + off, cnt, p, X_out, flags_out, fb, nullptr,
+                               perm_buf ? perm_buf + (size_t)off * F : nullptr);
+    };
+    // Three independent groups - split rows, warp rows, CTA-resident rows -
+    // write disjoint systems, masks and solutions: each assembles and then
+    // solves its own rows, the split-row chain (the longest dependent
+    // sequence) on the handle's high-priority stream, the warp rows on a
+    // second side stream, the CTA rows on the caller's stream, bucket by
+    // bucket, with each bucket's solve on a third side stream as soon as it
+    // is assembled (solves wait on latency, assemblies on issue slots). The
+    // side streams join before the refinement. Profiling keeps one stream,
+    // so that each launch's events time it alone.
+    const int groups = (pl.n_slots > 0) + (n_warp > 0) + (nb > 0);
+    const int buckets = (pl.n_bucket[0] > 0) + (pl.n_bucket[1] > 0) + (pl.n_bucket[2] > 0);
+    const bool overlap = (groups > 1 || buckets > 1) && !h->profiling;
+    if (overlap) {
+        rc = ensure_aux(h);
         if (rc) return rc;
-    } else if (mode == 1 && n_aug > 0) {
-        ALS_LAUNCH(h, "unpack_aug", als::k_unpack_aug<F><<<1024, 256, 0, st>>>(G_aug, lists, n_aug, p.f, G_out, b_out));
+        ALS_CUDA(h, cudaEventRecord(h->ev_fork, st));
     }
+    if (pl.n_slots > 0) {
+        if (overlap) {
+            ALS_CUDA(h, cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+            h->stream = h->aux;
+        }
+        rc = launch_split<F, ENG>(h, pl, side, p, mode, aug_split, masks_out);
+        if (!rc) rc = solve_range(off_split, pl.n_slots);
+        h->stream = st;
+        if (rc) return rc;
+        if (overlap) ALS_CUDA(h, cudaEventRecord(h->ev_join, h->aux));
+    }
+    if constexpr (F <= 32) {
+        if (n_warp > 0) {
+            if (overlap) {
+                ALS_CUDA(h, cudaStreamWaitEvent(h->aux2, h->ev_fork, 0));
+                h->stream = h->aux2;
+            }
+            rc = launch_warp_rows<F>(h, side, p, lists, n_warp, mode, masks_out, aug_warp);
+            if (!rc) rc = solve_range(0, n_warp);
+            h->stream = st;
+            if (rc) return rc;
+            if (overlap) ALS_CUDA(h, cudaEventRecord(h->ev_join2, h->aux2));
+        }
+    }
+    if (nb > 0) {
+        // Largest exponent per factor column: the top of the resident rows' CES window.
+        uint32_t* tcol = reinterpret_cast<uint32_t*>(static_cast<char*>(h->misc.p) + kColmaxOffset);
+        ALS_CUDA(h, cudaMemsetAsync(tcol, 0, (size_t)F * sizeof(uint32_t), st));
+        const int64_t total = side.n_cols * (int64_t)p.f;
+        const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)h->n_sm * 4));
+        ALS_LAUNCH(h, "colmax", als::k_colmax<F><<<blocks, 256, 0, st>>>(side.Y, side.n_cols, p.f, tcol));
+        for (int b = 2; b >= 0; --b) {
+            if (pl.n_bucket[b] == 0) continue;
+            float* aug = b == 2 ? aug_b2 : (b == 1 ? aug_b1 : aug_b0);
+            rc = launch_cta_bucket<F, ENG>(h, side, p, lists + pl.off_bucket(b),
+                                           pl.blen.data() + (pl.off_bucket(b) - pl.n_warp), pl.n_bucket[b], mode, aug,
+                                           masks_out, tcol);
+            if (rc) return rc;
+            if (overlap && mode == 0) {
+                ALS_CUDA(h, cudaEventRecord(h->ev_bucket[b], st));
+                ALS_CUDA(h, cudaStreamWaitEvent(h->aux3, h->ev_bucket[b], 0));
+                h->stream = h->aux3;
+            }
+            rc = solve_range(pl.off_bucket(b), pl.n_bucket[b]);
+            h->stream = st;
+            if (rc) return rc;
+        }
+        if (overlap && mode == 0) {
+            ALS_CUDA(h, cudaEventRecord(h->ev_join3, h->aux3));
+            ALS_CUDA(h, cudaStreamWaitEvent(st, h->ev_join3, 0));
+        }
+    }
+    if (overlap) {
+        if (pl.n_slots > 0) ALS_CUDA(h, cudaStreamWaitEvent(st, h->ev_join, 0));
+        if (F <= 32 && n_warp > 0) ALS_CUDA(h, cudaStreamWaitEvent(st, h->ev_join2, 0));
+    }
+    if (mode == 1 && n_aug > 0)
+        ALS_LAUNCH(h, "unpack_aug", als::k_unpack_aug<F><<<1024, 256, 0, st>>>(G_aug, lists, n_aug, p.f, G_out, b_out));
     // The CTA and split rows (contiguous after the warp rows) are refined;
     // warp rows always assemble in FP32 on CUDA cores.
     struct Seg { const int32_t* list; int count; float* aug; };
@@ -882,9 +934,11 @@ int als_destroy(als_handle* h) {
     }
     for (auto e : h->event_pool) cudaEventDestroy(e);
     if (h->fit_graph.exec) cudaGraphExecDestroy(h->fit_graph.exec);
-    if (h->aux) cudaStreamDestroy(h->aux);
-    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
-    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    for (cudaStream_t s : {h->aux, h->aux2, h->aux3})
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : {h->ev_fork, h->ev_join, h->ev_join2, h->ev_join3, h->ev_bucket[0], h->ev_bucket[1],
+                          h->ev_bucket[2]})
+        if (e) cudaEventDestroy(e);
     for (DevBuf* b : {&h->g_aug, &h->misc, &h->host_in, &h->masks, &h->fb_list, &h->delta, &h->perms})
         if (b->p) cudaFree(b->p);
     delete h;

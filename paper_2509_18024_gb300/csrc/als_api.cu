@@ -100,6 +100,7 @@ struct als_handle {
     // rows on aux2, the solves of the CTA-resident rows' buckets on aux3,
     // beside their assembly) and their fork/join events; made on first use.
     cudaStream_t aux = nullptr, aux2 = nullptr, aux3 = nullptr;
+    cudaStream_t copy = nullptr;  // host-to-device inputs of als_fit_host
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr, ev_join3 = nullptr;
     cudaEvent_t ev_bucket[3] = {nullptr, nullptr, nullptr};
     int device = 0;
@@ -458,6 +459,7 @@ int ensure_aux(als_handle* h) {
     if (!h->aux) ALS_CUDA(h, cudaStreamCreateWithPriority(&h->aux, cudaStreamNonBlocking, greatest));
     if (!h->aux2) ALS_CUDA(h, cudaStreamCreateWithPriority(&h->aux2, cudaStreamNonBlocking, least));
     if (!h->aux3) ALS_CUDA(h, cudaStreamCreateWithPriority(&h->aux3, cudaStreamNonBlocking, least));
+    if (!h->copy) ALS_CUDA(h, cudaStreamCreateWithPriority(&h->copy, cudaStreamNonBlocking, least));
     for (cudaEvent_t* e : {&h->ev_fork, &h->ev_join, &h->ev_join2, &h->ev_join3, &h->ev_bucket[0], &h->ev_bucket[1],
                            &h->ev_bucket[2]})
         if (!*e) ALS_CUDA(h, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
@@ -934,7 +936,7 @@ int als_destroy(als_handle* h) {
     }
     for (auto e : h->event_pool) cudaEventDestroy(e);
     if (h->fit_graph.exec) cudaGraphExecDestroy(h->fit_graph.exec);
-    for (cudaStream_t s : {h->aux, h->aux2, h->aux3})
+    for (cudaStream_t s : {h->aux, h->aux2, h->aux3, h->copy})
         if (s) cudaStreamDestroy(s);
     for (cudaEvent_t e : {h->ev_fork, h->ev_join, h->ev_join2, h->ev_join3, h->ev_bucket[0], h->ev_bucket[1],
                           h->ev_bucket[2]})
@@ -1172,9 +1174,23 @@ int als_fit_host(als_handle* h, int64_t n_u, int64_t n_m, int64_t nnz, const int
     const size_t s_uip = al((n_u + 1) * 8), s_iip = al((n_m + 1) * 8), s_ix = al(nnz * 4), s_v = al(nnz * 4);
     const size_t s_U = al(n_u * f * 4), s_M = al(n_m * f * 4), s_t = al(n_test * 4);
     const size_t total = s_uip + s_iip + 2 * s_ix + 2 * s_v + s_U + s_M + 3 * s_t;
+    const char* old_base = reinterpret_cast<const char*>(h->host_in.p);
+    const size_t old_bytes = h->host_in.bytes;
     int rc = ensure(h, h->host_in, total);
     if (rc) return rc;
     char* base = reinterpret_cast<char*>(h->host_in.p);
+    // This call refills the input buffer (perhaps moved): plans keyed on it
+    // must re-check its contents before use (kept when the row structure is
+    // unchanged), and the captured sweep, which may use them, is dropped.
+    for (Plan& p : h->plans) {
+        const char* q = reinterpret_cast<const char*>(p.indptr);
+        if ((old_base && q >= old_base && q < old_base + old_bytes) || (q >= base && q < base + h->host_in.bytes))
+            p.stale = true;
+    }
+    if (h->fit_graph.exec) {
+        cudaGraphExecDestroy(h->fit_graph.exec);
+        h->fit_graph = {};
+    }
     auto take = [&](size_t b) { char* p = base; base += b; return p; };
     int64_t* d_uip = (int64_t*)take(s_uip);
     int64_t* d_iip = (int64_t*)take(s_iip);
@@ -1188,37 +1204,58 @@ int als_fit_host(als_handle* h, int64_t n_u, int64_t n_m, int64_t nnz, const int
     int32_t* d_tm = (int32_t*)take(s_t);
     float* d_tr = (float*)take(s_t);
     cudaStream_t st = h->stream;
+    if (sweeps < 0) return set_err(h, ALS_ERR_ARG, "negative sweep count");
+    rc = ensure_aux(h);
+    if (rc) return rc;
+    // The user side and M^(0) go in on the caller's stream; the item side and
+    // the test set on the copy stream (after the stream's earlier work),
+    // where they are also validated while the first user half-sweep runs.
+    ALS_CUDA(h, cudaEventRecord(h->ev_fork, st));
+    ALS_CUDA(h, cudaStreamWaitEvent(h->copy, h->ev_fork, 0));
     ALS_CUDA(h, cudaMemcpyAsync(d_uip, uip, (n_u + 1) * 8, cudaMemcpyHostToDevice, st));
-    ALS_CUDA(h, cudaMemcpyAsync(d_iip, iip, (n_m + 1) * 8, cudaMemcpyHostToDevice, st));
+    ALS_CUDA(h, cudaMemcpyAsync(d_iip, iip, (n_m + 1) * 8, cudaMemcpyHostToDevice, h->copy));
     if (nnz > 0) {
         ALS_CUDA(h, cudaMemcpyAsync(d_uix, uix, nnz * 4, cudaMemcpyHostToDevice, st));
-        ALS_CUDA(h, cudaMemcpyAsync(d_iix, iix, nnz * 4, cudaMemcpyHostToDevice, st));
         ALS_CUDA(h, cudaMemcpyAsync(d_uv, uv, nnz * 4, cudaMemcpyHostToDevice, st));
-        ALS_CUDA(h, cudaMemcpyAsync(d_iv, iv, nnz * 4, cudaMemcpyHostToDevice, st));
+        ALS_CUDA(h, cudaMemcpyAsync(d_iix, iix, nnz * 4, cudaMemcpyHostToDevice, h->copy));
+        ALS_CUDA(h, cudaMemcpyAsync(d_iv, iv, nnz * 4, cudaMemcpyHostToDevice, h->copy));
     }
     ALS_CUDA(h, cudaMemcpyAsync(d_M, M_host, n_m * f * 4, cudaMemcpyHostToDevice, st));
     if (n_test > 0) {
-        ALS_CUDA(h, cudaMemcpyAsync(d_tu, tu, n_test * 4, cudaMemcpyHostToDevice, st));
-        ALS_CUDA(h, cudaMemcpyAsync(d_tm, tm, n_test * 4, cudaMemcpyHostToDevice, st));
-        ALS_CUDA(h, cudaMemcpyAsync(d_tr, tr, n_test * 4, cudaMemcpyHostToDevice, st));
+        ALS_CUDA(h, cudaMemcpyAsync(d_tu, tu, n_test * 4, cudaMemcpyHostToDevice, h->copy));
+        ALS_CUDA(h, cudaMemcpyAsync(d_tm, tm, n_test * 4, cudaMemcpyHostToDevice, h->copy));
+        ALS_CUDA(h, cudaMemcpyAsync(d_tr, tr, n_test * 4, cudaMemcpyHostToDevice, h->copy));
     }
     als_csr Ru{n_u, n_m, nnz, d_uip, d_uix, d_uv};
     als_csr Ri{n_m, n_u, nnz, d_iip, d_iix, d_iv};
+    int first = 0;  // sweeps done here (the first one, with the item side validated under it)
+    if (sweeps > 0) {
+        rc = als_half_sweep(h, &Ru, d_M, d_U, nullptr);
+        if (rc == ALS_OK) {
+            h->stream = h->copy;
+            rc = als_prepare(h, &Ri);
+            h->stream = st;
+        }
+        if (rc) {
+            cudaStreamSynchronize(h->copy);
+            return rc;
+        }
+        ALS_CUDA(h, cudaEventRecord(h->ev_join3, h->copy));
+        ALS_CUDA(h, cudaStreamWaitEvent(st, h->ev_join3, 0));
+        rc = als_half_sweep(h, &Ri, d_U, d_M, nullptr);
+        if (rc) return rc;
+        first = 1;
+    } else {
+        ALS_CUDA(h, cudaEventRecord(h->ev_join3, h->copy));
+        ALS_CUDA(h, cudaStreamWaitEvent(st, h->ev_join3, 0));
+    }
     als_report local;
-    rc = als_fit(h, &Ru, &Ri, sweeps, d_U, d_M, n_test, d_tu, d_tm, d_tr, rep ? rep : &local);
+    rc = als_fit(h, &Ru, &Ri, sweeps - first, d_U, d_M, n_test, d_tu, d_tm, d_tr, rep ? rep : &local);
     if (rc) return rc;
+    if (rep) rep->sweeps_done = sweeps;
     ALS_CUDA(h, cudaMemcpyAsync(U_host, d_U, n_u * f * 4, cudaMemcpyDeviceToHost, st));
     ALS_CUDA(h, cudaMemcpyAsync(M_host, d_M, n_m * f * 4, cudaMemcpyDeviceToHost, st));
     ALS_CUDA(h, cudaStreamSynchronize(st));
-    // The next call refills these device buffers: its plans must re-check
-    // the contents (kept when the row structure is unchanged), and the
-    // captured sweep is dropped.
-    if (h->fit_graph.exec) {
-        cudaGraphExecDestroy(h->fit_graph.exec);
-        h->fit_graph = {};
-    }
-    for (Plan& p : h->plans)
-        if (p.indptr == d_uip || p.indptr == d_iip) p.stale = true;
     return ALS_OK;
 }
 

@@ -253,6 +253,35 @@ def test_fit_host_equals_device_path(core, small):
     assert rep1["test_rmse"] == rep2["test_rmse"]
 
 
+def test_fit_host_pipelined_inputs(core, small):
+    # als_fit_host copies and validates the item side on its copy stream under
+    # the first user half-sweep: 0, 1 and 2 sweeps, repeated calls on the same
+    # structure (plans kept), and an invalid item side (rejected; the handle
+    # stays usable) all match the device-buffer path.
+    M0 = synth.init_factor(small.n_m, small.f, 1000)
+    test = (small.test_u, small.test_m, small.test_r)
+    eng = core.CoreALS(small.f, f32(0.1), 0.5)
+    Ru, Ri = core.DeviceCSR.from_host(small.train_rows), core.DeviceCSR.from_host(small.train_cols)
+    dtest = tuple(torch.as_tensor(a).cuda() for a in test)
+    for sweeps in (0, 1, 2, 2):
+        U1, M1, rep1 = eng.fit_host(small.train_rows, small.train_cols, M0, sweeps, test=test)
+        U2, M2, rep2 = eng.fit(Ru, Ri, torch.as_tensor(M0).cuda(), sweeps, test=dtest)
+        assert np.array_equal(M1, M2.cpu().numpy()), sweeps
+        assert rep1["sweeps_done"] == sweeps
+        if sweeps:  # (with none, U is the caller's initial buffer on each path)
+            assert np.array_equal(U1, U2.cpu().numpy()), sweeps
+            assert rep1["test_rmse"] == rep2["test_rmse"]
+    bad = small.train_cols
+    bad_idx = bad.indices.copy()
+    bad_idx[bad.indptr[1]] = small.n_u  # out of range in the second item row
+    bad = synth.CSR(bad.n_rows, bad.n_cols, bad.indptr, bad_idx, bad.values)
+    with pytest.raises(Exception, match="out of range"):
+        eng.fit_host(small.train_rows, bad, M0, 1, test=test)
+    U1, M1, _ = eng.fit_host(small.train_rows, small.train_cols, M0, 1, test=test)
+    U2, M2, _ = eng.fit(Ru, Ri, torch.as_tensor(M0).cuda(), 1, test=dtest)
+    assert np.array_equal(U1, U2.cpu().numpy()) and np.array_equal(M1, M2.cpu().numpy())
+
+
 def test_deterministic(core, small):
     M0 = torch.as_tensor(synth.init_factor(small.n_m, small.f, 5)).cuda()
     eng = core.CoreALS(small.f, 0.1, 0.5)

@@ -27,7 +27,12 @@
  *   - All work is enqueued on the handle's CUDA stream. Calls return when the
  *     work is enqueued, except where a _host output is filled (those
  *     synchronise the stream) and the first call on a new rating structure
- *     (see als_prepare).
+ *     (see als_prepare). Inside a half-sweep the handle forks independent
+ *     row groups onto side streams of its own (created on first use,
+ *     destroyed with the handle) and joins them back into the handle's
+ *     stream before the call's work ends on it: ordering against other work
+ *     on the handle's stream, and graph capture of that stream, are as if
+ *     everything ran on it.
  *   - The caller owns every buffer passed in; the library never frees caller
  *     memory. The handle owns its workspace (als_workspace_bytes).
  *   - Return value: ALS_OK (0) or a negative ALS_ERR_* code. Nothing is
@@ -211,7 +216,9 @@ int als_eval_sse_static(int64_t n, const int32_t* iu, const int32_t* im, const f
                         const float* M, int n_f, double* sse_dev, void* cuda_stream);
 
 /* Kernel timing: while enabled, every kernel the handle launches is
- * bracketed by CUDA events on the handle's stream. als_kernel_time
+ * bracketed by CUDA events on the handle's stream, and half-sweeps run on
+ * that stream alone (no side streams), so each event pair times one launch
+ * by itself; results are bit-identical either way. als_kernel_time
  * synchronises and returns the summed event time (ms) and the number of
  * launches of the kernels whose family name is `name` ("cta_rows",
  * "warp_rows", "solve_rows", "sse", ...) since profiling was enabled;
@@ -235,8 +242,12 @@ int als_fit(als_handle* h, const als_csr* R_users, const als_csr* R_items, int s
             const float* test_r, als_report* rep_host);
 
 /* als_fit from HOST buffers: copies both sides' CSR arrays, M^(0) and the
- * test entries to the device, fits, and copies U and M back to the host.
- * Uses the handle's workspace for device copies. */
+ * test entries to the device, fits, and copies U and M back to the host
+ * (synchronises). Uses the handle's workspace for device copies. The item
+ * side and the test entries go over a copy stream of the handle and the
+ * item side is validated there while the first user half-sweep runs; every
+ * host buffer is out of use when the call returns, also on error. Plans and
+ * the captured sweep tied to the workspace are re-checked on every call. */
 int als_fit_host(als_handle* h, int64_t n_u, int64_t n_m, int64_t nnz,
                  const int64_t* user_indptr_host, const int32_t* user_indices_host,
                  const float* user_values_host, const int64_t* item_indptr_host,

@@ -156,6 +156,8 @@ class CoreALS:
                    B.ptr(M), B.ptr(out))
 
     def profile(self, enable: bool = True):
+        """als_profile: time every launch with CUDA events (half-sweeps then
+        run on the handle's stream alone, without side streams)."""
         self._call(self.lib.als_profile, 1 if enable else 0)
 
     def kernel_time(self, family: str | None = None):

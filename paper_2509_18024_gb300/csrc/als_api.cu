@@ -22,7 +22,7 @@ using als::Side;
 
 // Row plan of one side: rows bucketed by length - warp rows (n_i <= 32, for
 // widths up to 32), three CTA-resident capacities and split rows (longer than
-// the largest capacity, cut into Gram chunks); each bucket sorted by length
+// the largest capacity, cut into Gram chunks); each group sorted by length
 // descending so the longest start first. Capacities by padded width F keep
 // the staged slice plus histograms within shared memory.
 struct BucketCaps {
@@ -369,6 +369,9 @@ int build_plan(als_handle* h, const als_csr* R, Plan** out) {
         else split_rows.push_back((int32_t)i);
     }
     auto longer = [&](int32_t a, int32_t b) { return indptr[a + 1] - indptr[a] > indptr[b + 1] - indptr[b]; };
+    // Warp rows by length too: the eight warps of a CTA then do similar work
+    // (a CTA's slot frees only when its slowest warp is done).
+    std::stable_sort(warp_rows.begin(), warp_rows.end(), longer);
     for (auto& v : bucket) std::stable_sort(v.begin(), v.end(), longer);
     std::stable_sort(split_rows.begin(), split_rows.end(), longer);
     std::vector<int32_t> c_begin(1, 0), ch_slot, ch_start, sc_slot, sc_start;

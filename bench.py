@@ -168,6 +168,20 @@ def reference_arm(args, p, w, M0, r):
 
 
 # ------------------------------------------------------------- GPU arm
+def replica_value(ms, rows, steps, world, device):
+    """Whole-job throughput of `world` independent replicas: every rank
+    solved `rows` rows per step for `steps` timed steps in `ms` (its own CUDA
+    events); the job's time is the slowest rank's, taken by an all-reduce
+    MAX over the process group (no other exchange). Returns (ms, value)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * rows * steps / (ms / 1e3)
+
+
 def gpu_arm(args, p, w, M0, r, rank, world, local_rank):
     import torch
     from paper_2509_18024_gb300 import core_als
@@ -228,12 +242,7 @@ def gpu_arm(args, p, w, M0, r, rank, world, local_rank):
         if n:
             fam[name] = (t, n)
     eng.profile(False)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    rows = (p.n_u + p.n_m)
-    value = world * rows * args.steps / (ms / 1e3)
+    ms, value = replica_value(ms, p.n_u + p.n_m, args.steps, world, dev)
     test_rmse = float(np.sqrt(sse.item() / len(p.test_r)))
 
     if rank != 0:

@@ -279,7 +279,7 @@ KERNEL_FAMILIES = ("cta_rows", "warp_rows", "solve_rows", "split_init", "split_h
 # `roofline.traffic` is that sum over the sweep's measured launches). It
 # holds only for the kernel sources it was taken from: `roofline.traffic` is
 # null once their hash differs.
-TRAFFIC = {"kernel": "cta_rows", "bytes_per_sweep": 295.3e6, "sources_sha256_16": "e4721848b63c82e5"}
+TRAFFIC = {"kernel": "cta_rows", "bytes_per_sweep": 295.3e6, "sources_sha256_16": "b7282143df965677"}
 
 
 def kernel_sources_hash():

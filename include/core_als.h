@@ -226,8 +226,20 @@ int als_eval_sse_static(int64_t n, const int32_t* iu, const int32_t* im, const f
 int als_profile(als_handle* h, int enable);
 int als_kernel_time(als_handle* h, const char* name, double* ms_host, int64_t* launches_host);
 
-/* Counters of the last half-sweep (synchronises). */
+/* Counters of the last half-sweep (synchronises). Returns ALS_ERR_TIMEOUT,
+ * with the report still filled, when a bounded device wait ran out since the
+ * last report: the tensor-core Gram pipelines give up on a completion
+ * barrier after 1 s of GPU time, zero the systems they were assembling and
+ * record the timeout in a device error word, which this call reads and
+ * clears (the handle stays usable; the results of the calls since the last
+ * report are not valid). als_fit and als_fit_host return it the same way. */
 int als_get_report(als_handle* h, als_report* rep_host);
+
+/* Self-test of that mechanism: one thread waits up to limit_ns (0..2e9) of
+ * GPU time on a barrier that nothing arrives at, records the timeout like
+ * the pipelines do, and the call returns ALS_ERR_TIMEOUT after reading and
+ * clearing the record (synchronises). Nothing faults or hangs. */
+int als_wait_selftest(als_handle* h, int64_t limit_ns);
 
 /* One full sweep: users from M (into U), then items from the new U (into M). */
 int als_sweep(als_handle* h, const als_csr* R_users, const als_csr* R_items, float* U, float* M);

@@ -78,6 +78,7 @@ SIGNATURES = {
     "als_profile": (C.c_int, [_P, C.c_int]),
     "als_kernel_time": (C.c_int, [_P, C.c_char_p, _P, _P]),
     "als_get_report": (C.c_int, [_P, _P]),
+    "als_wait_selftest": (C.c_int, [_P, C.c_int64]),
     "als_sweep": (C.c_int, [_P, _P, _P, _P, _P]),
     "als_fit": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, _I64, _P, _P, _P, _P]),
     "als_fit_host": (C.c_int, [_P, _I64, _I64, _I64, _P, _P, _P, _P, _P, _P, C.c_int, _P, _P, _I64, _P, _P,

@@ -250,6 +250,7 @@ Params make_params(const als_options& o) {
     p.reg_mode = o.reg_mode;
     p.gram_mode = o.gram_mode;
     p.ratio_max = (float)o.pivot_ratio_max;
+    p.err = nullptr;
     return p;
 }
 
@@ -293,7 +294,20 @@ double* eval_partials(als_handle* h) {
 double* eval_out(als_handle* h) { return eval_partials(h) + als::kEvalBlocks; }
 unsigned* valid_err(als_handle* h) { return reinterpret_cast<unsigned*>(eval_out(h) + 1); }
 constexpr size_t kColmaxOffset = 256 + (als::kEvalBlocks + 1) * sizeof(double) + 64;  // uint32[128]
-constexpr size_t kMiscBytes = kColmaxOffset + 128 * sizeof(uint32_t);
+constexpr size_t kDevErrOffset = kColmaxOffset + 128 * sizeof(uint32_t);
+constexpr size_t kMiscBytes = kDevErrOffset + 16;
+// Sticky device error word: bit 0 = a bounded device wait ran out. Kernels
+// set it; the host reads and clears it when it synchronises for a report.
+unsigned* dev_err(als_handle* h) { return reinterpret_cast<unsigned*>(static_cast<char*>(h->misc.p) + kDevErrOffset); }
+
+// Status of a device error word value read back by the host (which then clears the word).
+int dev_err_status(als_handle* h, unsigned e) {
+    if (e == 0) return ALS_OK;
+    ALS_CUDA(h, cudaMemsetAsync(dev_err(h), 0, sizeof(unsigned), h->stream));
+    return set_err(h, ALS_ERR_TIMEOUT,
+                   "a bounded device wait ran out (tensor-core completion barrier): results since the last report "
+                   "are not valid");
+}
 
 // Validate one side's structure on the device and download its indptr.
 int validate_csr(als_handle* h, const als_csr* R, std::vector<int64_t>& indptr) {
@@ -651,6 +665,7 @@ int run_side(als_handle* h, const Plan& pl, const Side& side, int mode, float* X
              uint32_t* masks_out, float* G_out, float* b_out) {
     cudaStream_t st = h->stream;
     Params p = make_params(h->opt);
+    p.err = dev_err(h);
     const int n_warp = F <= 32 ? pl.n_warp : 0;
     const int n_aug = n_warp + pl.n_cta_like();
     int rc = ensure(h, h->g_aug, (size_t)std::max(n_aug, 1) * F * (F + 1) * sizeof(float));
@@ -1068,7 +1083,9 @@ int als_kernel_time(als_handle* h, const char* name, double* ms_host, int64_t* l
 int als_get_report(als_handle* h, als_report* rep) {
     if (!h || !rep) return ALS_ERR_ARG;
     Counters c;
+    unsigned e = 0;
     ALS_CUDA(h, cudaMemcpyAsync(&c, counters(h), sizeof c, cudaMemcpyDeviceToHost, h->stream));
+    ALS_CUDA(h, cudaMemcpyAsync(&e, dev_err(h), sizeof e, cudaMemcpyDeviceToHost, h->stream));
     ALS_CUDA(h, cudaStreamSynchronize(h->stream));
     std::memset(rep, 0, sizeof *rep);
     rep->rows_flagged = (int64_t)c.flagged;
@@ -1079,7 +1096,17 @@ int als_get_report(als_handle* h, als_report* rep) {
     rep->max_pivot_ratio = mr;
     rep->test_rmse = NAN;
     rep->objective = NAN;
-    return ALS_OK;
+    return dev_err_status(h, e);
+}
+
+int als_wait_selftest(als_handle* h, int64_t limit_ns) {
+    if (!h) return ALS_ERR_ARG;
+    if (limit_ns < 0 || limit_ns > 2000000000ll) return set_err(h, ALS_ERR_ARG, "limit_ns must be in [0, 2e9]");
+    ALS_LAUNCH(h, "wait_selftest", als::k_wait_selftest<<<1, 32, 0, h->stream>>>((uint64_t)limit_ns, dev_err(h)));
+    unsigned e = 0;
+    ALS_CUDA(h, cudaMemcpyAsync(&e, dev_err(h), sizeof e, cudaMemcpyDeviceToHost, h->stream));
+    ALS_CUDA(h, cudaStreamSynchronize(h->stream));
+    return dev_err_status(h, e);
 }
 
 int als_sweep(als_handle* h, const als_csr* Ru, const als_csr* Ri, float* U, float* M) {

@@ -32,6 +32,7 @@ struct Params {
     int reg_mode;
     int gram_mode;
     float ratio_max;     // pivot-ratio flag threshold
+    unsigned* err;       // sticky device error word (bit 0: a bounded wait ran out), or null
 };
 
 struct Side {

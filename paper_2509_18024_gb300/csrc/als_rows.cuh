@@ -546,7 +546,7 @@ __global__ void __launch_bounds__(kCtaThreads, ENG == ENG_CUDA ? 4 : 1) k_cta_ro
     const bool sym = p.gram_mode == GRAM_SYM;
     TcPipe P;
     if constexpr (TC) {
-        if (mode != 2 && blockIdx.x < n_list) tc_pipe_setup<F, PREC>(s_tiles, s_bars, s_tmem, P);
+        if (mode != 2 && blockIdx.x < n_list) tc_pipe_setup<F, PREC>(s_tiles, s_bars, s_tmem, P, p.err);
     }
     // This warp's selection bins: zeroed once, every selection leaves them zero.
     uint32_t* const H = reinterpret_cast<uint32_t*>(s_u) + warp * kQuadHistWords;
@@ -886,7 +886,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_split_gram(Side side, Params p,
     const bool sym = p.gram_mode == GRAM_SYM;
     TcPipe P;
     if constexpr (TC) {
-        if (mode != 2 && blockIdx.x < sp.n_chunks) tc_pipe_setup<F, PREC>(S.tiles, S.bars, &S.tmem_slot, P);
+        if (mode != 2 && blockIdx.x < sp.n_chunks) tc_pipe_setup<F, PREC>(S.tiles, S.bars, &S.tmem_slot, P, p.err);
     }
     int prev_c = -1, prev_acc = 0, prev_len = 0, runs = 0;
     auto finish_prev = [&]() {

@@ -69,17 +69,46 @@ struct TcCtx {
     bool ok;         // false once a bounded wait ran out
 };
 
-// Bounded wait for the MMAs committed to `bar` (phase parity `phase`).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
+// Nanoseconds of the GPU's global timer.
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for phase parity `phase` of `bar` (the MMAs committed to it):
+// gives up after limit_ns of global time and returns false.
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s; an MMA batch completes in microseconds
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, uint64_t limit_ns = kWaitLimitNs) {
     uint32_t done = 0;
-    for (long it = 0; it < (1l << 24) && !done; ++it) {
+    const uint64_t t0 = global_ns();
+    for (;;) {
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
             : "=r"(done)
             : "r"(smem_addr(bar)), "r"(phase)
             : "memory");
+        if (done || global_ns() - t0 > limit_ns) break;
     }
     return done != 0;
+}
+
+// Records a bounded wait that ran out in the sticky device error word.
+constexpr unsigned kDevErrTimeout = 1u;
+__device__ __forceinline__ void report_timeout(unsigned* err) {
+    if (err) atomicOr(err, kDevErrTimeout);
+}
+
+// Self-test of the bounded wait: thread 0 waits on a fresh barrier that
+// nothing arrives at, so the wait runs out after limit_ns and is recorded in
+// the error word exactly as a timeout of the tensor-core pipelines is.
+__global__ void k_wait_selftest(uint64_t limit_ns, unsigned* err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar)));
+        if (!mbar_wait(&bar, 0u, limit_ns)) report_timeout(err);
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(&bar)));
+    }
 }
 
 // Write one 16-byte operand row (KC consecutive positions of one feature).
@@ -138,10 +167,12 @@ struct TcPipe {
     int pend[2];      // a commit on this buffer is outstanding
     int next;         // buffer the next chunk uses
     bool ok;          // false once a bounded wait ran out
+    unsigned* err;    // sticky device error word for such a timeout (or null)
 };
 
 template <int F, int PREC>
-__device__ __forceinline__ void tc_pipe_setup(uint8_t* tiles, uint64_t* bars, uint32_t* tmem_slot, TcPipe& P) {
+__device__ __forceinline__ void tc_pipe_setup(uint8_t* tiles, uint64_t* bars, uint32_t* tmem_slot, TcPipe& P,
+                                              unsigned* err) {
     using C = TcCfg<F, PREC>;
     const int tid = threadIdx.x, warp = tid >> 5;
     uint32_t* t32 = reinterpret_cast<uint32_t*>(tiles);
@@ -163,11 +194,17 @@ __device__ __forceinline__ void tc_pipe_setup(uint8_t* tiles, uint64_t* bars, ui
     P.pend[0] = P.pend[1] = 0;
     P.next = 0;
     P.ok = true;
+    P.err = err;
 }
 
 __device__ __forceinline__ void tc_pipe_drain(TcPipe& P, uint64_t* bars, int b) {
     if (P.pend[b]) {
-        if (!mbar_wait(&bars[b], P.ph[b])) P.ok = false;
+        if (!mbar_wait(&bars[b], P.ph[b])) {
+            // The rows of this CTA from here on store zeros and the host
+            // learns of it from the error word (ALS_ERR_TIMEOUT).
+            if (P.ok) report_timeout(P.err);
+            P.ok = false;
+        }
         P.ph[b] ^= 1u;
         P.pend[b] = 0;
     }

@@ -97,3 +97,25 @@ def test_refinement_keeps_fp32_at_parity(core):
     eng = core.CoreALS(32, lam, r, refine_steps=1)
     X = eng.half_sweep(core.DeviceCSR.from_host(csr), torch.as_tensor(Y).cuda()).cpu().numpy()
     assert rel_fro(X, Xo) <= 1e-5
+
+
+def test_bounded_wait_runs_out_reports_and_handle_stays_usable(core):
+    # A wait on a barrier that nothing arrives at gives up after its limit,
+    # the device error word records it, the host call returns
+    # ALS_ERR_TIMEOUT, and the record is cleared: the handle keeps working.
+    from paper_2509_18024_gb300 import binding as B
+    csr, Y = rows_problem([0, 5, 40, 300, 2000], 3000, 64, seed=41)
+    eng = core.CoreALS(64, 0.05, 0.25)
+    with pytest.raises(B.AlsError) as e:
+        eng._call(eng.lib.als_wait_selftest, 1_000_000)  # 1 ms of GPU time
+    assert e.value.status == -5 and B.STATUS[-5] == "ALS_ERR_TIMEOUT"
+    # Cleared: the next report is clean, and a half-sweep (tensor-core Gram
+    # at n_f = 64) still matches the oracle.
+    R = core.DeviceCSR.from_host(csr)
+    X = eng.half_sweep(R, torch.as_tensor(Y).cuda()).cpu().numpy()
+    eng.report()
+    Xo, _, _ = oracle.half_sweep(csr.indptr, csr.indices, csr.values, Y.astype(np.float64), f32(0.05), 0.25,
+                                 oracle.GRAM_ASYM)
+    assert rel_fro(X, Xo) <= 1e-5
+    with pytest.raises(B.AlsError):
+        eng._call(eng.lib.als_wait_selftest, -1)

@@ -321,3 +321,86 @@ def capture_case(name: str, f: int, seed: int = 0, n_cols: int = 30_000):
     vals = rng.standard_normal(int(lengths.sum())).astype(np.float32)
     Y = (rng.standard_normal((n_cols, f)) * 0.6).astype(np.float32)
     return CSR(n_rows, n_cols, indptr, idx.astype(np.int32), vals), Y
+
+
+# ---------------------------------------------------------------------------
+# The simulation design of Sec. 5.1: factors U (n_u x p) and M (n_m x p) with
+# i.i.d. rows from D1 N(0, Sigma), D2 the log-normal exp(N(0, Sigma)) or D3
+# the multivariate t with 4 degrees of freedom N(0, Sigma) / sqrt(chi2_4 / 4),
+# Sigma_ij = 0.6^|i - j|; R^o = U M^T; R = R^o + N(0, 1) noise on every cell;
+# then a fraction `missing` of the cells is removed at random. The removed
+# cells form the prediction set I^c (their values are those of R), the rest
+# the empirical set I used for fitting.
+#
+# Reading of a garbled point: the paper removes "(1 - alpha)" of the cells
+# yet calls alpha = 0.4 (R1) the dense case and alpha = 0.7 (R4) the sparse
+# one; `missing` = alpha is the fraction removed, which matches R1 dense,
+# R4 sparse.
+SIM_DISTRIBUTIONS = ("D1", "D2", "D3")
+SIM_MISSING = {"R1": 0.4, "R2": 0.5, "R3": 0.6, "R4": 0.7}
+
+
+@dataclass
+class SimulationProblem:
+    n_u: int
+    n_m: int
+    f: int
+    train_rows: CSR      # empirical set I, users x items
+    train_cols: CSR      # its transpose
+    pred_u: np.ndarray   # prediction set I^c: int32 users
+    pred_m: np.ndarray   # int32 items
+    pred_r: np.ndarray   # float32 values of R there
+    U_true: np.ndarray
+    M_true: np.ndarray
+
+
+def _sim_factor(n: int, p: int, dist: str, rng: np.random.Generator) -> np.ndarray:
+    idx = np.arange(p)
+    sigma = 0.6 ** np.abs(idx[:, None] - idx[None, :])
+    L = np.linalg.cholesky(sigma)
+    z = rng.standard_normal((n, p)) @ L.T
+    if dist == "D1":
+        return z
+    if dist == "D2":
+        return np.exp(z)
+    if dist == "D3":
+        w = rng.chisquare(4.0, size=(n, 1))
+        return z / np.sqrt(w / 4.0)
+    raise ValueError(f"unknown factor distribution {dist!r}")
+
+
+def simulation(dist: str = "D1", missing: float = 0.4, n_u: int = 3600, n_m: int = 3600, f: int = 60,
+               seed: int = 1) -> SimulationProblem:
+    rng = np.random.default_rng(seed)
+    U = _sim_factor(n_u, f, dist, rng)
+    M = _sim_factor(n_m, f, dist, rng)
+    R = U @ M.T + rng.standard_normal((n_u, n_m))
+    n_cells = n_u * n_m
+    n_miss = int(round(missing * n_cells))
+    gone = np.zeros(n_cells, bool)
+    gone[rng.choice(n_cells, size=n_miss, replace=False)] = True
+    cells = np.arange(n_cells, dtype=np.int64)
+    obs, mis = cells[~gone], cells[gone]
+    flat = R.reshape(-1)
+    ii, jj = obs // n_m, obs % n_m
+    rows = coo_to_csr(ii, jj, flat[obs].astype(np.float32), n_u, n_m)
+    cols = coo_to_csr(jj, ii, flat[obs].astype(np.float32), n_m, n_u)
+    return SimulationProblem(n_u, n_m, f, rows, cols, (mis // n_m).astype(np.int32), (mis % n_m).astype(np.int32),
+                             flat[mis].astype(np.float32), U, M)
+
+
+def relevant_items(n_u: int, n_m: int, test_u: np.ndarray, test_m: np.ndarray, test_r: np.ndarray,
+                   threshold: float) -> CSR:
+    """Per user, the held-out items whose true rating is at least `threshold`
+    (the items that should be recommended), as a CSR of sorted item ids."""
+    keep = np.asarray(test_r) >= threshold
+    u = np.asarray(test_u)[keep].astype(np.int64)
+    m = np.asarray(test_m)[keep].astype(np.int64)
+    return coo_to_csr(u, m, np.ones(u.shape[0], np.float32), n_u, n_m)
+
+
+def top_share_threshold(values: np.ndarray, share: float = 0.05) -> float:
+    """The value above which the largest `share` of `values` lie (the
+    relevance cut of the simulation's recommendation metrics)."""
+    v = np.sort(np.asarray(values, np.float64))
+    return float(v[int(np.floor((1.0 - share) * (v.shape[0] - 1)))]) if v.size else np.inf

@@ -89,6 +89,16 @@ extern "C" {
  * tracks the FP32 one (BF16 rounds to 8 significant bits, TF32 to 11). */
 #define ALS_REFINE_AUTO (-1)
 
+/* Sketch of a row's design slice:
+ *   ALS_SKETCH_SLICE   Algorithm 2: CES (Algorithm 1) on every row's slice.
+ *   ALS_SKETCH_FACTOR  the fast variant of Sec. 3: CES once per half-sweep on
+ *                      the whole design factor Y (n_cols rows, the budget
+ *                      rule evaluated at n = n_cols, ties to the lower row of
+ *                      Y); a row's sketch is that selection restricted to its
+ *                      slice, so a row keeps the rate only on average. */
+#define ALS_SKETCH_SLICE 0
+#define ALS_SKETCH_FACTOR 1
+
 #define ALS_FLAG_RATIO 1     /* pivot ratio above pivot_ratio_max */
 #define ALS_FLAG_SINGULAR 2  /* zero / non-positive pivot: the row was set to 0 */
 #define ALS_FLAG_FP64 4      /* the row was re-assembled and re-solved in FP64 */
@@ -119,6 +129,10 @@ typedef struct als_options {
                                 or ALS_REFINE_AUTO): each recomputes the residual
                                 of the FP32 system from the data and solves the
                                 assembled G again (CTA and split rows) */
+    int64_t fixed_keep;      /* 0: the rate rule s_i = floor(n_i r); > 0: the
+                                fixed subsample size of Sec. 3, s_i =
+                                min(n_i, fixed_keep) per column (budget unused) */
+    int sketch;              /* ALS_SKETCH_SLICE or ALS_SKETCH_FACTOR */
 } als_options;
 
 typedef struct als_report {
@@ -127,7 +141,8 @@ typedef struct als_report {
     int64_t rows_fp64;        /* rows re-solved in FP64, last half-sweep */
     double max_pivot_ratio;   /* largest pivot ratio seen, last half-sweep */
     double test_rmse;         /* als_fit: test RMSE after the last sweep (NaN if no test set) */
-    double objective;         /* als_fit: Eq. (object function) after the last sweep */
+    double objective;         /* als_fit: Eq. (object function) after the last sweep, with the
+                                 handle's regulariser mode (NaN from als_get_report) */
     int sweeps_done;
 } als_report;
 
@@ -135,7 +150,8 @@ typedef struct als_handle als_handle;
 
 /* Default options: n_f = 32, lambda = 0.05, budget = 0.25, weighted lambda,
  * asymmetric Gram, FP32, pivot_ratio_max = 1e6, FP64 fallback on,
- * refine_steps = ALS_REFINE_AUTO. */
+ * refine_steps = ALS_REFINE_AUTO, the rate rule (fixed_keep = 0), the
+ * per-slice sketch of Algorithm 2. */
 void als_default_options(als_options* opt_host);
 
 /* Create a handle bound to the current CUDA device and to cuda_stream
@@ -204,7 +220,9 @@ int als_eval_sse_async(als_handle* h, int64_t n, const int32_t* iu, const int32_
  * ALS_SSE_STATIC_MAX_ENTRIES (2^26): larger n returns ALS_ERR_ARG and
  * enqueues nothing.
  * The first call on a device looks up the array's device address with that
- * device current. Make this first call before any stream capture.
+ * device current, and caches it per (device, CUDA context): a call under a
+ * new context (after cudaDeviceReset, for instance) looks it up again. Make
+ * the first call in a context before any stream capture.
  * All calls share the one array. A call writes every partial it later reads,
  * so nothing carries over from a previous call. Calls that overlap on the GPU
  * (other streams or threads) race on the array and must be serialised by the
@@ -214,6 +232,39 @@ int als_eval_sse_async(als_handle* h, int64_t n, const int32_t* iu, const int32_
 #define ALS_SSE_STATIC_MAX_ENTRIES ((int64_t)ALS_SSE_STATIC_MAX_BLOCKS * ALS_SSE_STATIC_ENTRIES_PER_BLOCK)
 int als_eval_sse_static(int64_t n, const int32_t* iu, const int32_t* im, const float* r, const float* U,
                         const float* M, int n_f, double* sse_dev, void* cuda_stream);
+
+/* Eq. (object function) at (U, M): sum over the training entries of R_users
+ * of (r_ij - u_i . m_j)^2 plus lambda (sum_i n_i |u_i|^2 + sum_j n_j |m_j|^2)
+ * with the handle's lambda and weighted regulariser (n_i, n_j the row counts
+ * of R_users and R_items), or lambda (sum_i |u_i|^2 + sum_j |m_j|^2) with
+ * ALS_REG_PLAIN. Products FP32, sums FP64 in a fixed order. Synchronises.
+ * Only R_items' indptr is read. */
+int als_objective(als_handle* h, const als_csr* R_users, const als_csr* R_items, const float* U, const float* M,
+                  double* obj_host);
+
+/* Relative error of Sec. 5.1 over n entries E: sqrt(sum_E (r - u_i . m_j)^2)
+ * / sqrt(sum_E r^2) - ReMSE on the empirical (training) set, P-ReMSE on the
+ * prediction (missing) set - for one replication. Synchronises; NaN for an
+ * empty set. */
+int als_eval_remse(als_handle* h, int64_t n, const int32_t* iu, const int32_t* im, const float* r, const float* U,
+                   const float* M, double* remse_host);
+
+/* Recommendation metrics of Sec. 5.1. For every user i (row of R_train, the
+ * training ratings), the items not rated in R_train are ranked by the FP32
+ * predicted rating u_i . m_j (products accumulated by fmaf in feature order;
+ * ties: lower item first) and the first K = max(k_hit, k_ndcg) <= 16 are
+ * kept (topk_out, nullable: n_u x K int32, -1 when fewer items are unrated).
+ * Against each user's relevant items (rel: CSR over the same users, sorted
+ * item ids, e.g. held-out items rated at least a threshold): Hit@k_hit is 1
+ * when one of the first k_hit items is relevant; NDCG@k_ndcg = DCG / IDCG
+ * with binary gains, DCG = sum_p rel_p / log2(p + 2) over positions p =
+ * 0..k_ndcg-1, IDCG the same with min(k_ndcg, |rel_i|) relevant items in
+ * front. The means over users with at least one relevant item go to
+ * hit_host and ndcg_host, their number to n_eval_host (nullable).
+ * Synchronises. R_train.n_cols (the items) may be at most 1,500,000. */
+int als_eval_ranking(als_handle* h, const als_csr* R_train, const als_csr* rel, const float* U, const float* M,
+                     int k_hit, int k_ndcg, int32_t* topk_out, double* hit_host, double* ndcg_host,
+                     int64_t* n_eval_host);
 
 /* Kernel timing: while enabled, every kernel the handle launches is
  * bracketed by CUDA events on the handle's stream, and half-sweeps run on
@@ -228,27 +279,37 @@ int als_kernel_time(als_handle* h, const char* name, double* ms_host, int64_t* l
 
 /* Counters of the last half-sweep (synchronises). Returns ALS_ERR_TIMEOUT,
  * with the report still filled, when a bounded device wait ran out since the
- * last report: the tensor-core Gram pipelines give up on a completion
- * barrier after 1 s of GPU time, zero the systems they were assembling and
- * record the timeout in a device error word, which this call reads and
- * clears (the handle stays usable; the results of the calls since the last
- * report are not valid). als_fit and als_fit_host return it the same way. */
+ * last report: a tensor-core Gram pipeline that gives up on a completion
+ * barrier after 1 s of GPU time stops issuing work, waits once more (bounded)
+ * for what it had in flight, frees its tensor memory, stores zero systems and
+ * records the timeout in a device error word, which this call reads and
+ * clears. After ALS_ERR_TIMEOUT the results of the calls since the last
+ * report are undefined; destroy the handle and create a new one before
+ * relying on it again. als_fit, als_fit_host and als_batch_fit return it the
+ * same way. */
 int als_get_report(als_handle* h, als_report* rep_host);
 
 /* Self-test of that mechanism: one thread waits up to limit_ns (0..2e9) of
- * GPU time on a barrier that nothing arrives at, records the timeout like
- * the pipelines do, and the call returns ALS_ERR_TIMEOUT after reading and
- * clearing the record (synchronises). Nothing faults or hangs. */
-int als_wait_selftest(als_handle* h, int64_t limit_ns);
+ * GPU time on a barrier that nothing arrives at and records the timeout like
+ * the pipelines do. keep_record 0: the call synchronises, reads and clears
+ * the record and returns ALS_ERR_TIMEOUT. keep_record 1: the call only
+ * enqueues the wait and returns ALS_OK, leaving the record for the next call
+ * that reads it (als_get_report, als_fit, als_fit_host). Nothing faults or
+ * hangs. */
+int als_wait_selftest(als_handle* h, int64_t limit_ns, int keep_record);
 
 /* One full sweep: users from M (into U), then items from the new U (into M). */
 int als_sweep(als_handle* h, const als_csr* R_users, const als_csr* R_items, float* U, float* M);
 
 /* Algorithm 2: `sweeps` sweeps starting from M (in: M^(0), out: result);
- * U is output only. If test entries are given (n_test > 0) the report gets
- * the test RMSE after the last sweep. rep_host nullable. On a created
- * stream, after the first sweep the remaining sweeps replay a CUDA graph of
- * one sweep (captured on the first call with these buffers). */
+ * U is output only. rep_host nullable; when given it gets the counters of
+ * the last half-sweep, the objective of Eq. (object function) after the last
+ * sweep (als_objective) and, if test entries are given (n_test > 0), the
+ * test RMSE. On a created stream, after the first sweep the remaining sweeps
+ * replay a CUDA graph of one sweep (captured on the first call with these
+ * buffers). The call always ends by synchronising the stream to read the
+ * device error word (also when rep_host is NULL), so a bounded device wait
+ * that ran out during the fit returns ALS_ERR_TIMEOUT. */
 int als_fit(als_handle* h, const als_csr* R_users, const als_csr* R_items, int sweeps,
             float* U, float* M, int64_t n_test, const int32_t* test_u, const int32_t* test_m,
             const float* test_r, als_report* rep_host);
@@ -306,7 +367,8 @@ int als_get_tuning(const als_handle* h, als_tuning* t_host);
  * interact, so each problem's result equals the one it gets alone. One
  * sweep of all groups is captured into a CUDA graph and replayed. Options
  * other than n_f come from opt; cuda_stream must not be the legacy default
- * stream (graph capture needs a created stream). */
+ * stream (graph capture needs a created stream). The fast variant
+ * (ALS_SKETCH_FACTOR) is not built for batches: ALS_ERR_UNSUPPORTED. */
 typedef struct als_problem {
     als_csr users;  /* R in CSR (device arrays) */
     als_csr items;  /* R^T in CSR (device arrays) */
@@ -322,8 +384,17 @@ typedef struct als_batch als_batch;
 int als_batch_create(als_batch** batch_host, const als_options* opt_host, int n_problems,
                      const als_problem* problems_host, void* cuda_stream);
 /* `sweeps` sweeps of Algorithm 2 for every problem from its M (read at the
- * start), writing U and M back. Enqueued on the batch stream. */
+ * start), writing U and M back. Enqueued on the batch stream; the call then
+ * synchronises it to read every width group's device error word and returns
+ * ALS_ERR_TIMEOUT if a bounded device wait ran out in any group. */
 int als_batch_fit(als_batch* b, int sweeps);
+/* CES masks (as als_select) of one side (0 users, 1 items) of problem
+ * `problem`, computed on the batch's block-diagonal structure with that
+ * problem's design factor Y (device, the other side's rows x n_f; copied into
+ * the batch's factor buffer, which the next als_batch_fit overwrites).
+ * masks_out: the problem's nnz x ceil(n_f/32) words in its own CSR order.
+ * Synchronises. */
+int als_batch_select(als_batch* b, int problem, int side, const float* Y, uint32_t* masks_out);
 /* Kernel launches in one replayed sweep (all groups). */
 int64_t als_batch_launches_per_sweep(const als_batch* b);
 int als_batch_destroy(als_batch* b);

@@ -23,6 +23,7 @@ ALS_GRAM_ASYM, ALS_GRAM_SYM, ALS_GRAM_FULL = 0, 1, 2
 ALS_FP32, ALS_TF32, ALS_BF16, ALS_FP32_TC = 0, 1, 2, 3
 ALS_FLAG_RATIO, ALS_FLAG_SINGULAR, ALS_FLAG_FP64 = 1, 2, 4
 ALS_REFINE_AUTO = -1
+ALS_SKETCH_SLICE, ALS_SKETCH_FACTOR = 0, 1
 ALS_SSE_STATIC_MAX_ENTRIES = 4096 * 16384
 
 
@@ -40,7 +41,8 @@ class als_csr(C.Structure):
 class als_options(C.Structure):
     _fields_ = [("n_f", C.c_int), ("lambda_", C.c_float), ("budget", C.c_double), ("min_keep", C.c_int64),
                 ("reg_mode", C.c_int), ("gram_mode", C.c_int), ("precision", C.c_int),
-                ("pivot_ratio_max", C.c_double), ("fp64_fallback", C.c_int), ("refine_steps", C.c_int)]
+                ("pivot_ratio_max", C.c_double), ("fp64_fallback", C.c_int), ("refine_steps", C.c_int),
+                ("fixed_keep", C.c_int64), ("sketch", C.c_int)]
 
 
 class als_report(C.Structure):
@@ -75,10 +77,13 @@ SIGNATURES = {
     "als_eval_sse": (C.c_int, [_P, _I64, _P, _P, _P, _P, _P, _P]),
     "als_eval_sse_async": (C.c_int, [_P, _I64, _P, _P, _P, _P, _P, _P]),
     "als_eval_sse_static": (C.c_int, [_I64, _P, _P, _P, _P, _P, C.c_int, _P, _P]),
+    "als_objective": (C.c_int, [_P, _P, _P, _P, _P, _P]),
+    "als_eval_remse": (C.c_int, [_P, _I64, _P, _P, _P, _P, _P, _P]),
+    "als_eval_ranking": (C.c_int, [_P, _P, _P, _P, _P, C.c_int, C.c_int, _P, _P, _P, _P]),
     "als_profile": (C.c_int, [_P, C.c_int]),
     "als_kernel_time": (C.c_int, [_P, C.c_char_p, _P, _P]),
     "als_get_report": (C.c_int, [_P, _P]),
-    "als_wait_selftest": (C.c_int, [_P, C.c_int64]),
+    "als_wait_selftest": (C.c_int, [_P, C.c_int64, C.c_int]),
     "als_sweep": (C.c_int, [_P, _P, _P, _P, _P]),
     "als_fit": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, _I64, _P, _P, _P, _P]),
     "als_fit_host": (C.c_int, [_P, _I64, _I64, _I64, _P, _P, _P, _P, _P, _P, C.c_int, _P, _P, _I64, _P, _P,
@@ -88,6 +93,7 @@ SIGNATURES = {
     "als_get_tuning": (C.c_int, [_P, _P]),
     "als_batch_create": (C.c_int, [_P, _P, C.c_int, _P, _P]),
     "als_batch_fit": (C.c_int, [_P, C.c_int]),
+    "als_batch_select": (C.c_int, [_P, C.c_int, C.c_int, _P, _P]),
     "als_batch_launches_per_sweep": (_I64, [_P]),
     "als_batch_destroy": (C.c_int, [_P]),
     "als_features": (C.c_int, [_P, _P, C.c_int, _P, _P]),

@@ -15,6 +15,7 @@ import torch
 from . import binding as B
 
 GRAM_MODES = {"asym": B.ALS_GRAM_ASYM, "sym": B.ALS_GRAM_SYM, "full": B.ALS_GRAM_FULL}
+SKETCHES = {"slice": B.ALS_SKETCH_SLICE, "factor": B.ALS_SKETCH_FACTOR}
 REG_MODES = {"weighted": B.ALS_REG_WEIGHTED, "plain": B.ALS_REG_PLAIN}
 
 
@@ -54,7 +55,8 @@ class CoreALS:
 
     def __init__(self, n_f: int, lam: float, budget: float, gram_mode: str = "asym",
                  reg_mode: str = "weighted", min_keep: int = 0, ratio_max: float = 1e6,
-                 precision: int = B.ALS_FP32, fp64_fallback: bool = True, refine_steps: int = B.ALS_REFINE_AUTO):
+                 precision: int = B.ALS_FP32, fp64_fallback: bool = True, refine_steps: int = B.ALS_REFINE_AUTO,
+                 fixed_keep: int = 0, sketch: str = "slice"):
         _require_cuda()
         self.lib = B.load()
         opt = B.als_options()
@@ -69,6 +71,8 @@ class CoreALS:
         opt.pivot_ratio_max = float(ratio_max)
         opt.fp64_fallback = 1 if fp64_fallback else 0
         opt.refine_steps = int(refine_steps)
+        opt.fixed_keep = int(fixed_keep)
+        opt.sketch = SKETCHES[sketch]
         self.opt = opt
         self.n_f = int(n_f)
         h = C.c_void_p()
@@ -155,6 +159,31 @@ class CoreALS:
         self._call(self.lib.als_eval_sse_async, int(r.shape[0]), B.ptr(iu), B.ptr(im), B.ptr(r), B.ptr(U),
                    B.ptr(M), B.ptr(out))
 
+    def objective(self, Ru: DeviceCSR, Ri: DeviceCSR, U: torch.Tensor, M: torch.Tensor) -> float:
+        """Eq. (object function) at (U, M) with the handle's lambda and regulariser."""
+        out = C.c_double()
+        self._call(self.lib.als_objective, C.byref(Ru.c_struct()), C.byref(Ri.c_struct()), B.ptr(U), B.ptr(M),
+                   C.byref(out))
+        return out.value
+
+    def remse(self, iu, im, r, U, M) -> float:
+        """Sec. 5.1 relative error over the listed entries (ReMSE / P-ReMSE)."""
+        out = C.c_double()
+        self._call(self.lib.als_eval_remse, int(r.shape[0]), B.ptr(iu), B.ptr(im), B.ptr(r), B.ptr(U), B.ptr(M),
+                   C.byref(out))
+        return out.value
+
+    def ranking(self, R_train: DeviceCSR, rel: DeviceCSR, U, M, k_hit: int = 5, k_ndcg: int = 10,
+                want_lists: bool = False):
+        """(Hit@k_hit, NDCG@k_ndcg, users evaluated[, lists]) of Sec. 5.1."""
+        K = max(k_hit, k_ndcg)
+        lists = torch.empty((R_train.n_rows, K), dtype=torch.int32, device=U.device) if want_lists else None
+        hit, ndcg, n = C.c_double(), C.c_double(), C.c_int64()
+        self._call(self.lib.als_eval_ranking, C.byref(R_train.c_struct()), C.byref(rel.c_struct()), B.ptr(U),
+                   B.ptr(M), int(k_hit), int(k_ndcg), B.ptr(lists), C.byref(hit), C.byref(ndcg), C.byref(n))
+        out = (hit.value, ndcg.value, n.value)
+        return out + (lists,) if want_lists else out
+
     def profile(self, enable: bool = True):
         """als_profile: time every launch with CUDA events (half-sweeps then
         run on the handle's stream alone, without side streams)."""
@@ -235,7 +264,7 @@ class CoreBatch:
 
     def __init__(self, problems, lam: float, budget: float, gram_mode: str = "asym", reg_mode: str = "weighted",
                  precision: int = B.ALS_FP32, fp64_fallback: bool = True, refine_steps: int = B.ALS_REFINE_AUTO,
-                 stream=None):
+                 stream=None, fixed_keep: int = 0, sketch: str = "slice"):
         _require_cuda()
         self.lib = B.load()
         opt = B.als_options()
@@ -247,6 +276,8 @@ class CoreBatch:
         opt.precision = int(precision)
         opt.fp64_fallback = 1 if fp64_fallback else 0
         opt.refine_steps = int(refine_steps)
+        opt.fixed_keep = int(fixed_keep)
+        opt.sketch = SKETCHES[sketch]
         self.stream = stream if stream is not None else torch.cuda.Stream()
         self.problems = problems  # keep the tensors alive
         arr = (B.als_problem * len(problems))()
@@ -261,6 +292,14 @@ class CoreBatch:
     @property
     def launches_per_sweep(self) -> int:
         return int(self.lib.als_batch_launches_per_sweep(self.b))
+
+    def select(self, q: int, side: int, Y: torch.Tensor) -> torch.Tensor:
+        """CES masks of problem q's side (0 users, 1 items) from the batched
+        structure, with that problem's design factor Y."""
+        Ru, Ri, n_f = self.problems[q][:3]
+        masks = torch.zeros(((Ru if side == 0 else Ri).nnz, (n_f + 31) // 32), dtype=torch.int32, device=Y.device)
+        B.check(self.lib.als_batch_select(self.b, int(q), int(side), B.ptr(Y.contiguous()), B.ptr(masks)))
+        return masks
 
     def fit(self, sweeps: int):
         B.check(self.lib.als_batch_fit(self.b, int(sweeps)))

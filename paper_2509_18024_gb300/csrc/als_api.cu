@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "core_als.h"
+#include "als_eval.h"
 #include "als_fp64.cuh"
 #include "als_kernels.cuh"
 
@@ -67,10 +68,11 @@ void free_plan(Plan& p) {
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-// Layout of Plan::d_split for width F.
+// Layout of Plan::d_split for width F (with_part false: no chunk Grams, for
+// the fast variant's factor-wide selection, which assembles nothing).
 struct SplitLayout {
     size_t P, Mk, need, cut, done, ghist, arrive, eqc, part, total;
-    SplitLayout(int n_slots, int n_chunks, int F) {
+    SplitLayout(int n_slots, int n_chunks, int F, bool with_part = true) {
         size_t o = 0;
         const size_t sc = (size_t)std::max(n_slots, 1) * F * 4;
         P = o; o += align256(sc);
@@ -81,7 +83,7 @@ struct SplitLayout {
         ghist = o; o += align256(sc * 256);
         arrive = o; o += align256((size_t)std::max(n_slots, 1) * 4);
         eqc = o; o += align256((size_t)std::max(n_chunks, 1) * F * 4);
-        part = o; o += align256((size_t)std::max(n_chunks, 1) * F * (F + 1) * 4);
+        part = o; o += with_part ? align256((size_t)std::max(n_chunks, 1) * F * (F + 1) * 4) : 256;
         total = o;
     }
 };
@@ -89,6 +91,20 @@ struct SplitLayout {
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
+};
+
+// Workspace of the fast variant's factor-wide selection for a factor of
+// n_cols rows at width F: the split-row selection runs on one virtual row
+// that holds every row of the factor once (indices 0..n_cols-1).
+struct FactorWs {
+    int64_t n_cols = -1;
+    int F = 0;
+    void* mem = nullptr;
+    int n_chunks = 0, n_super = 0;
+    int64_t* vip = nullptr;     // {0, n_cols}
+    int32_t* iota = nullptr;    // 0..n_cols-1
+    int32_t* lists = nullptr;   // [row | c_begin | ch_slot | ch_start | sc_slot | sc_start]
+    void* split = nullptr;      // SplitLayout(1, n_chunks, F, false)
 };
 
 }  // namespace
@@ -113,6 +129,8 @@ struct als_handle {
     DevBuf fb_list;   // rows flagged for the FP64 redo
     DevBuf delta;     // refinement corrections
     DevBuf perms;     // pivot permutations of the stored LU factors (n_f > 32, refinement)
+    DevBuf evalbuf;   // partial sums of the objective, ReMSE and ranking kernels
+    std::vector<FactorWs> fws;  // fast-variant selection workspaces (by factor size and width)
     int n_sm = 152;
     int64_t launches = 0;
     std::string last_error;
@@ -227,6 +245,7 @@ int padded_width(int f, int precision) {
 
 // Padded width the plans and kernels of a handle use (its options and tuning).
 int plan_width(const ::als_handle* h);
+int factor_ws(::als_handle* h, int64_t n_cols, int F, FactorWs** out);
 
 // Gram engine for an option set: FP32 runs on CUDA cores up to 32 features
 // and as split TF32 on tensor cores above; the other precisions always use
@@ -250,7 +269,11 @@ Params make_params(const als_options& o) {
     p.reg_mode = o.reg_mode;
     p.gram_mode = o.gram_mode;
     p.ratio_max = (float)o.pivot_ratio_max;
+    p.fixed_keep = o.fixed_keep;
     p.err = nullptr;
+    p.gP = nullptr;
+    p.gMk = nullptr;
+    p.gcut = nullptr;
     return p;
 }
 
@@ -268,6 +291,9 @@ int check_options(als_handle* h, const als_options* o) {
     if (o->fp64_fallback != 0 && o->fp64_fallback != 1) return set_err(h, ALS_ERR_ARG, "fp64_fallback must be 0 or 1");
     if (o->refine_steps < ALS_REFINE_AUTO || o->refine_steps > 3)
         return set_err(h, ALS_ERR_ARG, "refine_steps must be ALS_REFINE_AUTO or 0 to 3");
+    if (o->fixed_keep < 0) return set_err(h, ALS_ERR_ARG, "fixed_keep must be >= 0");
+    if (o->sketch != ALS_SKETCH_SLICE && o->sketch != ALS_SKETCH_FACTOR)
+        return set_err(h, ALS_ERR_ARG, "sketch must be ALS_SKETCH_SLICE or ALS_SKETCH_FACTOR");
     return ALS_OK;
 }
 
@@ -453,6 +479,13 @@ int build_plan(als_handle* h, const als_csr* R, Plan** out) {
     }
     h->plans.push_back(p);
     *out = &h->plans.back();
+    // The fast variant's selection workspace for this side's design factor,
+    // made here so that captured sweeps find it.
+    if (h->opt.sketch == ALS_SKETCH_FACTOR && h->opt.gram_mode != ALS_GRAM_FULL && R->n_cols > 0) {
+        FactorWs* w = nullptr;
+        int rc = factor_ws(h, R->n_cols, F, &w);
+        if (rc) return rc;
+    }
     return ALS_OK;
 }
 
@@ -570,6 +603,130 @@ void split_views(const Plan& pl, int F, als::SplitPlan& sp, als::SplitState& ss)
     ss.part = reinterpret_cast<float*>(mem + L.part);
 }
 
+// The radix selection of the split rows (per slot and column): init, four
+// histogram passes, equal-key counts, the positional cut.
+template <int F>
+int launch_split_select(als_handle* h, const Side& side, const Params& p, const als::SplitPlan& sp,
+                        const als::SplitState& ss, const char* fam_hist) {
+    cudaStream_t st = h->stream;
+    const int sc = sp.n_slots * F;
+    ALS_LAUNCH(h, "split_init", als::k_split_init<F><<<(sc + 255) / 256, 256, 0, st>>>(side, p, sp, ss));
+    constexpr int CG = als::split_hist_cols(F);
+    const size_t hsmem = (size_t)CG * als::kHistRow * 4;
+    ALS_CUDA(h, cudaFuncSetAttribute(als::k_split_hist<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem));
+    for (int pass = 0; pass < 4; ++pass) {
+        ALS_LAUNCH(h, fam_hist, als::k_split_hist<F><<<sp.n_super * (F / CG), als::kCtaThreads, hsmem, st>>>(
+                                    side, p, sp, ss, pass));
+    }
+    ALS_LAUNCH(h, "split_eqcount", als::k_split_eqcount<F><<<sp.n_chunks, als::kCtaThreads, 0, st>>>(side, p, sp, ss));
+    ALS_LAUNCH(h, "split_cut", als::k_split_cut<F><<<(sc * 32 + 255) / 256, 256, 0, st>>>(side, p, sp, ss));
+    return ALS_OK;
+}
+
+__global__ void k_iota(int32_t* __restrict__ dst, int64_t n) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        dst[e] = (int32_t)e;
+}
+
+// The fast variant's selection workspace for a factor of n_cols rows at
+// width F (built once, synchronising; a few are kept).
+int factor_ws(als_handle* h, int64_t n_cols, int F, FactorWs** out) {
+    for (auto& w : h->fws)
+        if (w.n_cols == n_cols && w.F == F) {
+            *out = &w;
+            return ALS_OK;
+        }
+    FactorWs w;
+    w.n_cols = n_cols;
+    w.F = F;
+    const int chunk = als::split_chunk(F);
+    w.n_chunks = (int)((n_cols + chunk - 1) / chunk);
+    w.n_super = (int)((n_cols + als::kSplitSuper - 1) / als::kSplitSuper);
+    std::vector<int32_t> lists = {0, 0, w.n_chunks};  // row, c_begin
+    for (int c = 0; c < w.n_chunks; ++c) lists.push_back(0);
+    for (int c = 0; c < w.n_chunks; ++c) lists.push_back(c * chunk);
+    for (int q = 0; q < w.n_super; ++q) lists.push_back(0);
+    for (int q = 0; q < w.n_super; ++q) lists.push_back(q * als::kSplitSuper);
+    const SplitLayout L(1, w.n_chunks, F, false);
+    const size_t s_iota = align256((size_t)n_cols * 4), s_lists = align256(lists.size() * 4);
+    if (cudaMalloc(&w.mem, 256 + s_iota + s_lists + L.total) != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(h, ALS_ERR_OOM, "cudaMalloc(fast-variant selection workspace) failed");
+    }
+    char* base = static_cast<char*>(w.mem);
+    w.vip = reinterpret_cast<int64_t*>(base);
+    w.iota = reinterpret_cast<int32_t*>(base + 256);
+    w.lists = reinterpret_cast<int32_t*>(base + 256 + s_iota);
+    w.split = base + 256 + s_iota + s_lists;
+    const int64_t vip[2] = {0, n_cols};
+    cudaStream_t st = h->stream;
+    int rc = ALS_OK;
+    if (cudaMemcpyAsync(w.vip, vip, sizeof vip, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(w.lists, lists.data(), lists.size() * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(static_cast<char*>(w.split) + L.ghist, 0, L.eqc - L.ghist, st) != cudaSuccess)
+        rc = ALS_ERR_CUDA;
+    if (rc == ALS_OK) {
+        k_iota<<<(int)std::min<int64_t>((n_cols + 255) / 256, 4096), 256, 0, st>>>(w.iota, n_cols);
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) rc = ALS_ERR_CUDA;
+    }
+    if (rc) {
+        cudaGetLastError();
+        cudaFree(w.mem);
+        return set_err(h, rc, "building the fast-variant selection workspace failed");
+    }
+    if (h->fws.size() >= 4) {
+        cudaStreamSynchronize(st);
+        cudaFree(h->fws.front().mem);
+        h->fws.erase(h->fws.begin());
+    }
+    h->fws.push_back(w);
+    *out = &h->fws.back();
+    return ALS_OK;
+}
+
+// Fast variant (Sec. 3): CES once on the whole design factor Y - the split
+// selection on the virtual row of all of Y's rows, budget rule at n =
+// n_cols - and its keep rule handed to every row kernel through p.
+template <int F>
+int launch_factor_sketch(als_handle* h, const Side& side, Params& p) {
+    FactorWs* w = nullptr;
+    int rc = factor_ws(h, side.n_cols, F, &w);
+    if (rc) return rc;
+    Side vs = side;
+    vs.indptr = w->vip;
+    vs.indices = w->iota;
+    vs.values = nullptr;
+    vs.n_rows = 1;
+    als::SplitPlan sp;
+    sp.row = w->lists;
+    sp.c_begin = sp.row + 1;
+    sp.ch_slot = sp.c_begin + 2;
+    sp.ch_start = sp.ch_slot + w->n_chunks;
+    sp.sc_slot = sp.ch_start + w->n_chunks;
+    sp.sc_start = sp.sc_slot + w->n_super;
+    sp.n_slots = 1;
+    sp.n_chunks = w->n_chunks;
+    sp.n_super = w->n_super;
+    const SplitLayout L(1, w->n_chunks, F, false);
+    char* mem = static_cast<char*>(w->split);
+    als::SplitState ss;
+    ss.P = reinterpret_cast<uint32_t*>(mem + L.P);
+    ss.Mk = reinterpret_cast<uint32_t*>(mem + L.Mk);
+    ss.need = reinterpret_cast<int32_t*>(mem + L.need);
+    ss.cut = reinterpret_cast<int32_t*>(mem + L.cut);
+    ss.done = reinterpret_cast<int32_t*>(mem + L.done);
+    ss.ghist = reinterpret_cast<uint32_t*>(mem + L.ghist);
+    ss.arrive = reinterpret_cast<int32_t*>(mem + L.arrive);
+    ss.eqc = reinterpret_cast<int32_t*>(mem + L.eqc);
+    ss.part = reinterpret_cast<float*>(mem + L.part);
+    rc = launch_split_select<F>(h, vs, p, sp, ss, "factor_hist");
+    if (rc) return rc;
+    p.gP = ss.P;
+    p.gMk = ss.Mk;
+    p.gcut = ss.cut;
+    return ALS_OK;
+}
+
 template <int F, int ENG>
 int launch_split(als_handle* h, const Plan& pl, const Side& side, const Params& p, int mode, float* G_aug,
                  uint32_t* masks_out) {
@@ -578,17 +735,11 @@ int launch_split(als_handle* h, const Plan& pl, const Side& side, const Params& 
     als::SplitPlan sp;
     als::SplitState ss;
     split_views(pl, F, sp, ss);
-    const int sc = pl.n_slots * F;
-    ALS_LAUNCH(h, "split_init", als::k_split_init<F><<<(sc + 255) / 256, 256, 0, st>>>(side, p, sp, ss));
-    constexpr int CG = als::split_hist_cols(F);
-    const size_t hsmem = (size_t)CG * als::kHistRow * 4;
-    ALS_CUDA(h, cudaFuncSetAttribute(als::k_split_hist<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem));
-    for (int pass = 0; pass < 4; ++pass) {
-        ALS_LAUNCH(h, "split_hist", als::k_split_hist<F><<<pl.n_super * (F / CG), als::kCtaThreads, hsmem, st>>>(
-                                        side, p, sp, ss, pass));
+    // The fast variant's rows take the factor-wide rule: no selection here.
+    if (p.gP == nullptr) {
+        int rc = launch_split_select<F>(h, side, p, sp, ss, "split_hist");
+        if (rc) return rc;
     }
-    ALS_LAUNCH(h, "split_eqcount", als::k_split_eqcount<F><<<pl.n_chunks, als::kCtaThreads, 0, st>>>(side, p, sp, ss));
-    ALS_LAUNCH(h, "split_cut", als::k_split_cut<F><<<(sc * 32 + 255) / 256, 256, 0, st>>>(side, p, sp, ss));
     auto gkern = als::k_split_gram<F, ENG>;
     size_t smem = sizeof(als::SplitGramSmem<F, ENG>);
     ALS_CUDA(h, cudaFuncSetAttribute(gkern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -666,6 +817,10 @@ int run_side(als_handle* h, const Plan& pl, const Side& side, int mode, float* X
     cudaStream_t st = h->stream;
     Params p = make_params(h->opt);
     p.err = dev_err(h);
+    if (h->opt.sketch == ALS_SKETCH_FACTOR && h->opt.gram_mode != ALS_GRAM_FULL && side.n_cols > 0) {
+        const int src = launch_factor_sketch<F>(h, side, p);
+        if (src) return src;
+    }
     const int n_warp = F <= 32 ? pl.n_warp : 0;
     const int n_aug = n_warp + pl.n_cta_like();
     int rc = ensure(h, h->g_aug, (size_t)std::max(n_aug, 1) * F * (F + 1) * sizeof(float));
@@ -756,10 +911,12 @@ int run_side(als_handle* h, const Plan& pl, const Side& side, int mode, float* X
     if (nb > 0) {
         // Largest exponent per factor column: the top of the resident rows' CES window.
         uint32_t* tcol = reinterpret_cast<uint32_t*>(static_cast<char*>(h->misc.p) + kColmaxOffset);
-        ALS_CUDA(h, cudaMemsetAsync(tcol, 0, (size_t)F * sizeof(uint32_t), st));
-        const int64_t total = side.n_cols * (int64_t)p.f;
-        const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)h->n_sm * 4));
-        ALS_LAUNCH(h, "colmax", als::k_colmax<F><<<blocks, 256, 0, st>>>(side.Y, side.n_cols, p.f, tcol));
+        if (p.gP == nullptr) {  // the fast variant selects nothing per row
+            ALS_CUDA(h, cudaMemsetAsync(tcol, 0, (size_t)F * sizeof(uint32_t), st));
+            const int64_t total = side.n_cols * (int64_t)p.f;
+            const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)h->n_sm * 4));
+            ALS_LAUNCH(h, "colmax", als::k_colmax<F><<<blocks, 256, 0, st>>>(side.Y, side.n_cols, p.f, tcol));
+        }
         for (int b = 2; b >= 0; --b) {
             if (pl.n_bucket[b] == 0) continue;
             float* aug = b == 2 ? aug_b2 : (b == 1 ? aug_b1 : aug_b0);
@@ -959,8 +1116,9 @@ int als_destroy(als_handle* h) {
     for (cudaEvent_t e : {h->ev_fork, h->ev_join, h->ev_join2, h->ev_join3, h->ev_bucket[0], h->ev_bucket[1],
                           h->ev_bucket[2]})
         if (e) cudaEventDestroy(e);
-    for (DevBuf* b : {&h->g_aug, &h->misc, &h->host_in, &h->masks, &h->fb_list, &h->delta, &h->perms})
+    for (DevBuf* b : {&h->g_aug, &h->misc, &h->host_in, &h->masks, &h->fb_list, &h->delta, &h->perms, &h->evalbuf})
         if (b->p) cudaFree(b->p);
+    for (auto& w : h->fws) cudaFree(w.mem);
     delete h;
     return ALS_OK;
 }
@@ -1051,6 +1209,91 @@ int als_eval_sse_async(als_handle* h, int64_t n, const int32_t* iu, const int32_
     return ALS_OK;
 }
 
+int als_objective(als_handle* h, const als_csr* Ru, const als_csr* Ri, const float* U, const float* M,
+                  double* obj_host) {
+    if (!h || !obj_host) return ALS_ERR_ARG;
+    int rc = check_csr(h, Ru);
+    if (!rc) rc = check_csr(h, Ri);
+    if (rc) return rc;
+    if (Ru->n_rows != Ri->n_cols || Ru->n_cols != Ri->n_rows || Ru->nnz != Ri->nnz)
+        return set_err(h, ALS_ERR_ARG, "user and item sides do not describe the same matrix");
+    if ((Ru->n_rows > 0 && !U) || (Ri->n_rows > 0 && !M)) return set_err(h, ALS_ERR_ARG, "null factor");
+    rc = ensure(h, h->evalbuf, (3 * als_eval::kBlocks + 8) * sizeof(double));
+    if (rc) return rc;
+    double* part = static_cast<double*>(h->evalbuf.p);
+    double* out = part + 3 * als_eval::kBlocks;
+    cudaStream_t st = h->stream;
+    cudaError_t e = als_eval::objective(st, Ru->indptr, Ru->indices, Ru->values, Ru->n_rows, Ri->indptr, Ri->n_rows,
+                                        U, M, h->opt.n_f, (double)h->opt.lambda,
+                                        h->opt.reg_mode == ALS_REG_PLAIN ? 1 : 0, part, out);
+    h->launches += 4;
+    if (e != cudaSuccess) return set_err(h, ALS_ERR_CUDA, "objective launch failed: %s", cudaGetErrorString(e));
+    ALS_CUDA(h, cudaMemcpyAsync(obj_host, out, sizeof(double), cudaMemcpyDeviceToHost, st));
+    ALS_CUDA(h, cudaStreamSynchronize(st));
+    return ALS_OK;
+}
+
+int als_eval_remse(als_handle* h, int64_t n, const int32_t* iu, const int32_t* im, const float* r, const float* U,
+                   const float* M, double* remse_host) {
+    if (!h || !remse_host) return ALS_ERR_ARG;
+    if (n < 0) return set_err(h, ALS_ERR_ARG, "negative count");
+    if (n == 0) {
+        *remse_host = NAN;
+        return ALS_OK;
+    }
+    if (!iu || !im || !r || !U || !M) return set_err(h, ALS_ERR_ARG, "null buffer");
+    int rc = ensure(h, h->evalbuf, (3 * als_eval::kBlocks + 8) * sizeof(double));
+    if (rc) return rc;
+    double* part = static_cast<double*>(h->evalbuf.p);
+    double* out = part + 3 * als_eval::kBlocks;
+    cudaStream_t st = h->stream;
+    cudaError_t e = als_eval::sse_and_norm(st, n, iu, im, r, U, M, h->opt.n_f, part, out);
+    h->launches += 2;
+    if (e != cudaSuccess) return set_err(h, ALS_ERR_CUDA, "ReMSE launch failed: %s", cudaGetErrorString(e));
+    double sums[2] = {0.0, 0.0};
+    ALS_CUDA(h, cudaMemcpyAsync(sums, out, sizeof sums, cudaMemcpyDeviceToHost, st));
+    ALS_CUDA(h, cudaStreamSynchronize(st));
+    *remse_host = sums[1] > 0.0 ? std::sqrt(sums[0]) / std::sqrt(sums[1]) : NAN;
+    return ALS_OK;
+}
+
+int als_eval_ranking(als_handle* h, const als_csr* Rt, const als_csr* rel, const float* U, const float* M,
+                     int k_hit, int k_ndcg, int32_t* topk_out, double* hit_host, double* ndcg_host,
+                     int64_t* n_eval_host) {
+    if (!h || !hit_host || !ndcg_host) return ALS_ERR_ARG;
+    int rc = check_csr(h, Rt);
+    if (!rc) rc = check_csr(h, rel);
+    if (rc) return rc;
+    if (rel->n_rows != Rt->n_rows) return set_err(h, ALS_ERR_ARG, "relevant sets must cover the same users");
+    if (k_hit < 1 || k_ndcg < 1 || k_hit > als_eval::kRankMaxK || k_ndcg > als_eval::kRankMaxK)
+        return set_err(h, ALS_ERR_ARG, "k_hit and k_ndcg must be in 1..%d", als_eval::kRankMaxK);
+    if (Rt->n_cols > 1500000) return set_err(h, ALS_ERR_UNSUPPORTED, "more than 1,500,000 items");
+    if ((Rt->n_rows > 0 && !U) || (Rt->n_cols > 0 && !M)) return set_err(h, ALS_ERR_ARG, "null factor");
+    const int K = std::max(k_hit, k_ndcg);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(Rt->n_rows, (int64_t)h->n_sm * 4));
+    rc = ensure(h, h->evalbuf, (3 * (size_t)std::max(grid, als_eval::kBlocks) + 8) * sizeof(double));
+    if (rc) return rc;
+    double* part = static_cast<double*>(h->evalbuf.p);
+    double* out = part + 3 * std::max(grid, als_eval::kBlocks);
+    cudaStream_t st = h->stream;
+    if (Rt->n_rows == 0) {
+        *hit_host = *ndcg_host = NAN;
+        if (n_eval_host) *n_eval_host = 0;
+        return ALS_OK;
+    }
+    cudaError_t e = als_eval::rank(st, grid, Rt->n_rows, Rt->n_cols, h->opt.n_f, U, M, Rt->indptr, Rt->indices,
+                                   rel->indptr, rel->indices, K, k_hit, k_ndcg, topk_out, part, out);
+    h->launches += 2;
+    if (e != cudaSuccess) return set_err(h, ALS_ERR_CUDA, "ranking launch failed: %s", cudaGetErrorString(e));
+    double sums[3] = {0.0, 0.0, 0.0};
+    ALS_CUDA(h, cudaMemcpyAsync(sums, out, sizeof sums, cudaMemcpyDeviceToHost, st));
+    ALS_CUDA(h, cudaStreamSynchronize(st));
+    *hit_host = sums[2] > 0 ? sums[0] / sums[2] : NAN;
+    *ndcg_host = sums[2] > 0 ? sums[1] / sums[2] : NAN;
+    if (n_eval_host) *n_eval_host = (int64_t)sums[2];
+    return ALS_OK;
+}
+
 int als_profile(als_handle* h, int enable) {
     if (!h) return ALS_ERR_ARG;
     ALS_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -1099,10 +1342,11 @@ int als_get_report(als_handle* h, als_report* rep) {
     return dev_err_status(h, e);
 }
 
-int als_wait_selftest(als_handle* h, int64_t limit_ns) {
+int als_wait_selftest(als_handle* h, int64_t limit_ns, int keep_record) {
     if (!h) return ALS_ERR_ARG;
     if (limit_ns < 0 || limit_ns > 2000000000ll) return set_err(h, ALS_ERR_ARG, "limit_ns must be in [0, 2e9]");
     ALS_LAUNCH(h, "wait_selftest", als::k_wait_selftest<<<1, 32, 0, h->stream>>>((uint64_t)limit_ns, dev_err(h)));
+    if (keep_record) return ALS_OK;  // the next report-reading call returns the timeout
     unsigned e = 0;
     ALS_CUDA(h, cudaMemcpyAsync(&e, dev_err(h), sizeof e, cudaMemcpyDeviceToHost, h->stream));
     ALS_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -1178,9 +1422,13 @@ int als_fit(als_handle* h, const als_csr* Ru, const als_csr* Ri, int sweeps, flo
         int rc = als_sweep(h, Ru, Ri, U, M);
         if (rc) return rc;
     }
+    // Always read (and clear) the device error word: a bounded wait that ran
+    // out during these sweeps must not pass as ALS_OK.
+    als_report local;
+    als_report* rp = rep ? rep : &local;
+    int rc = als_get_report(h, rp);
+    if (rc) return rc;
     if (rep) {
-        int rc = als_get_report(h, rep);
-        if (rc) return rc;
         rep->sweeps_done = sweeps;
         if (n_test > 0) {
             double sse = 0.0;
@@ -1188,6 +1436,8 @@ int als_fit(als_handle* h, const als_csr* Ru, const als_csr* Ri, int sweeps, flo
             if (rc) return rc;
             rep->test_rmse = std::sqrt(sse / (double)n_test);
         }
+        rc = als_objective(h, Ru, Ri, U, M, &rep->objective);
+        if (rc) return rc;
     }
     return ALS_OK;
 }
@@ -1332,9 +1582,32 @@ static __device__ __align__(256) double g_sse_static_partials[ALS_SSE_STATIC_MAX
 constexpr int kStaticMaxDevices = 64;
 std::mutex g_sse_static_mu;
 double* g_sse_static_addr[kStaticMaxDevices] = {};
+void* g_sse_static_ctx[kStaticMaxDevices] = {};  // the context each address was looked up in
 
-// Device address of the scratch array on the current device, looked up once
-// per device (cudaGetSymbolAddress with that device current).
+// The current CUDA context (the driver's cuCtxGetCurrent, reached through the
+// runtime's entry-point query so that nothing links libcuda directly).
+using CtxGetCurrentFn = int (*)(void**);
+void* current_context() {
+    static CtxGetCurrentFn fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<CtxGetCurrentFn>(p);
+        else
+            cudaGetLastError();
+    }
+    void* ctx = nullptr;
+    if (fn == nullptr || fn(&ctx) != 0) return nullptr;
+    return ctx;
+}
+
+// Device address of the scratch array on the current device, looked up with
+// that device current (cudaGetSymbolAddress) once per (device, context): a
+// new context, e.g. after cudaDeviceReset, gets a new lookup.
 int sse_static_scratch(double** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -1343,13 +1616,15 @@ int sse_static_scratch(double** out) {
     }
     if (dev < 0 || dev >= kStaticMaxDevices) return ALS_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> lock(g_sse_static_mu);
-    if (g_sse_static_addr[dev] == nullptr) {
+    void* ctx = current_context();
+    if (g_sse_static_addr[dev] == nullptr || ctx == nullptr || ctx != g_sse_static_ctx[dev]) {
         void* ptr = nullptr;
         if (cudaGetSymbolAddress(&ptr, g_sse_static_partials) != cudaSuccess || ptr == nullptr) {
             cudaGetLastError();
             return ALS_ERR_CUDA;
         }
         g_sse_static_addr[dev] = static_cast<double*>(ptr);
+        g_sse_static_ctx[dev] = ctx;
     }
     *out = g_sse_static_addr[dev];
     return ALS_OK;
@@ -1547,6 +1822,9 @@ extern "C" int als_batch_create(als_batch** out, const als_options* opt, int n, 
     if (!out || !opt || n <= 0 || !probs) return ALS_ERR_ARG;
     *out = nullptr;
     if (stream == nullptr) return ALS_ERR_ARG;  // capture needs a created stream
+    // The fast variant selects over a whole factor; a block-diagonal stack
+    // would mix the problems' factors in one selection.
+    if (opt->sketch == ALS_SKETCH_FACTOR) return ALS_ERR_UNSUPPORTED;
     als_batch* b = new als_batch();
     b->stream = reinterpret_cast<cudaStream_t>(stream);
     b->probs.assign(probs, probs + n);
@@ -1677,10 +1955,69 @@ extern "C" int als_batch_fit(als_batch* b, int sweeps) {
                                 st) != cudaSuccess)
                 return ALS_ERR_CUDA;
         }
-    return ALS_OK;
+    // Every group's device error word: one small copy each, one synchronisation.
+    std::vector<unsigned> words(b->groups.size(), 0u);
+    for (size_t q = 0; q < b->groups.size(); ++q)
+        if (cudaMemcpyAsync(&words[q], dev_err(b->groups[q].h), sizeof(unsigned), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess)
+            return ALS_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return ALS_ERR_CUDA;
+    int status = ALS_OK;
+    for (size_t q = 0; q < b->groups.size(); ++q)
+        if (words[q] != 0u) {
+            const cudaStream_t hs = b->groups[q].h->stream;
+            b->groups[q].h->stream = st;
+            dev_err_status(b->groups[q].h, words[q]);  // clears the word
+            b->groups[q].h->stream = hs;
+            status = ALS_ERR_TIMEOUT;
+        }
+    return status;
 }
 
 extern "C" int64_t als_batch_launches_per_sweep(const als_batch* b) { return b ? b->launches : 0; }
+
+extern "C" int als_batch_select(als_batch* b, int problem, int side, const float* Y, uint32_t* masks_out) {
+    if (!b || problem < 0 || problem >= (int)b->probs.size() || (side != 0 && side != 1) || !Y || !masks_out)
+        return ALS_ERR_ARG;
+    BatchGroup* grp = nullptr;
+    size_t k = 0;
+    for (auto& g : b->groups)
+        for (size_t q = 0; q < g.members.size(); ++q)
+            if (g.members[q] == problem) {
+                grp = &g;
+                k = q;
+            }
+    if (!grp) return ALS_ERR_ARG;
+    const als_problem& pr = b->probs[problem];
+    const als_csr& R = side == 0 ? grp->users : grp->items;
+    const int64_t other_rows = side == 0 ? pr.items.n_rows : pr.users.n_rows;
+    const int64_t other_off = side == 0 ? grp->m_off[k] : grp->u_off[k];
+    const int W = (grp->n_f + 31) / 32;
+    int64_t e0 = 0;
+    for (size_t q = 0; q < k; ++q) e0 += b->probs[grp->members[q]].users.nnz;
+    // The group's design factor with this problem's rows taken from Y (the
+    // other problems' rows are left as they are: rows never interact).
+    float* Yg = side == 0 ? grp->M : grp->U;
+    cudaStream_t st = b->stream;
+    if (cudaMemcpyAsync(Yg + other_off * grp->n_f, Y, (size_t)other_rows * grp->n_f * 4, cudaMemcpyDeviceToDevice,
+                        st) != cudaSuccess)
+        return ALS_ERR_CUDA;
+    uint32_t* all = nullptr;
+    if (cudaMalloc(&all, (size_t)std::max<int64_t>(R.nnz, 1) * W * 4) != cudaSuccess) {
+        cudaGetLastError();
+        return ALS_ERR_OOM;
+    }
+    const cudaStream_t hs = grp->h->stream;
+    grp->h->stream = st;
+    int rc = als_select(grp->h, &R, Yg, all);
+    grp->h->stream = hs;
+    if (rc == ALS_OK && cudaMemcpyAsync(masks_out, all + e0 * W, (size_t)pr.users.nnz * W * 4, cudaMemcpyDeviceToDevice,
+                                        st) != cudaSuccess)
+        rc = ALS_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess && rc == ALS_OK) rc = ALS_ERR_CUDA;
+    cudaFree(all);
+    return rc;
+}
 
 extern "C" int als_batch_destroy(als_batch* b) {
     if (!b) return ALS_ERR_ARG;

@@ -29,10 +29,17 @@ struct Params {
     float lambda;
     double budget;       // r
     long long min_keep;  // 0 = off
+    long long fixed_keep;  // 0 = the rate rule; > 0: fixed subsample size
     int reg_mode;
     int gram_mode;
     float ratio_max;     // pivot-ratio flag threshold
     unsigned* err;       // sticky device error word (bit 0: a bounded wait ran out), or null
+    // Fast variant (CES once on the whole design factor Y): the keep rule of
+    // each column over Y's rows, positions being Y's row indices. Null: the
+    // per-slice CES of Algorithm 2.
+    const uint32_t* gP;
+    const uint32_t* gMk;
+    const int32_t* gcut;
 };
 
 struct Side {
@@ -67,11 +74,17 @@ struct Fallback {
 __device__ __forceinline__ uint32_t mag_key(float x) { return __float_as_uint(x) & 0x7fffffffu; }
 
 // s_i = floor(n_i * r) in IEEE double (the same expression as the oracle),
-// optionally raised to min_keep; n_i for the full update.
+// or min(n_i, fixed_keep) for a fixed subsample size; optionally raised to
+// min_keep; n_i for the full update.
 __device__ __forceinline__ long long row_budget(long long n, const Params& p) {
     if (p.gram_mode == GRAM_FULL) return n;
-    double prod = (double)n * p.budget;
-    long long s = (long long)floor(prod);
+    long long s;
+    if (p.fixed_keep > 0) {
+        s = p.fixed_keep < n ? p.fixed_keep : n;
+    } else {
+        double prod = (double)n * p.budget;
+        s = (long long)floor(prod);
+    }
     if (s > n) s = n;
     if (s < 0) s = 0;
     if (p.min_keep > 0 && s < p.min_keep) s = p.min_keep < n ? p.min_keep : n;

@@ -60,14 +60,24 @@ __global__ void __launch_bounds__(256, 4) k_warp_rows(Side side, Params p, const
     }
     __syncwarp();
 
-    const int s = (int)row_budget(n, p);
-    for (int a = 0; a < F; ++a) {
-        unsigned m = 0u;
-        if (a < f) {
-            uint32_t key = (lane < n) ? mag_key(T.u.x[lane][a]) : 0u;
-            m = warp_ces_column(key, n, s);
+    if (p.gP != nullptr) {
+        // Fast variant: the factor-wide keep rule, positions = rows of Y.
+        const int32_t j = lane < n ? T.idx[lane] : 0;
+        for (int a = 0; a < F; ++a) {
+            const bool kp = a < f && lane < n && keep_rule(mag_key(T.u.x[lane][a]), p.gP[a], p.gMk[a], j, p.gcut[a]);
+            const unsigned m = __ballot_sync(kFull, kp);
+            if (lane == 0) T.sel[a] = m;
         }
-        if (lane == 0) T.sel[a] = m;
+    } else {
+        const int s = (int)row_budget(n, p);
+        for (int a = 0; a < F; ++a) {
+            unsigned m = 0u;
+            if (a < f) {
+                uint32_t key = (lane < n) ? mag_key(T.u.x[lane][a]) : 0u;
+                m = warp_ces_column(key, n, s);
+            }
+            if (lane == 0) T.sel[a] = m;
+        }
     }
     __syncwarp();
     if (masks_out != nullptr && lane < n) {

@@ -200,10 +200,12 @@ __device__ __forceinline__ void init_column(int a, int f, long long s, long long
 // columns 4g..4g+3 (state P, Mk, cut indexed by column) to one float4 of
 // position k; the nibbles of one mask word meet by an OR over the (up to 8)
 // neighbouring lanes of that position. pos0 = position of tile row 0 in its
-// row.
+// row; with gpos (the fast variant's factor-wide rule) the position of tile
+// row k is gpos[k], its row index in the design factor.
 template <int F>
 __device__ __forceinline__ void build_masks(uint32_t (*mask)[MaskWords<F>::value], const float (*x)[xpitch(F)], int cn,
-                                            int pos0, const uint32_t* P, const uint32_t* Mk, const int32_t* cut) {
+                                            int pos0, const uint32_t* P, const uint32_t* Mk, const int32_t* cut,
+                                            const int32_t* gpos = nullptr) {
     static_assert(F % 4 == 0 && F / 4 <= 32, "a position's quarters sit in one warp");
     constexpr int T4 = F / 4;                  // threads per position
     constexpr int GW = T4 < 8 ? T4 : 8;        // threads per mask word
@@ -223,7 +225,7 @@ __device__ __forceinline__ void build_masks(uint32_t (*mask)[MaskWords<F>::value
         uint32_t nib = 0u;
         if (k < cn) {
             const float4 v = reinterpret_cast<const float4*>(x[k])[g];
-            const int pos = pos0 + k;
+            const int pos = gpos ? gpos[k] : pos0 + k;
             nib = (uint32_t)keep_rule(mag_key(v.x), Pc[0], Mc[0], pos, Cc[0]) |
                   ((uint32_t)keep_rule(mag_key(v.y), Pc[1], Mc[1], pos, Cc[1]) << 1) |
                   ((uint32_t)keep_rule(mag_key(v.z), Pc[2], Mc[2], pos, Cc[2]) << 2) |
@@ -552,6 +554,14 @@ __global__ void __launch_bounds__(kCtaThreads, ENG == ENG_CUDA ? 4 : 1) k_cta_ro
     uint32_t* const H = reinterpret_cast<uint32_t*>(s_u) + warp * kQuadHistWords;
     for (int e = lane; e < kQuadHistWords / 4; e += 32) reinterpret_cast<uint4*>(H)[e] = make_uint4(0u, 0u, 0u, 0u);
     __syncwarp();
+    // Fast variant: every row applies the factor-wide keep rule.
+    const bool factor_rule = p.gP != nullptr;
+    if (factor_rule)
+        for (int a = tid; a < F; a += kCtaThreads) {
+            s_P[a] = p.gP[a];
+            s_Mk[a] = p.gMk[a];
+            s_cut[a] = p.gcut[a];
+        }
     int prev_w = -1, prev_n = 0, prev_acc = 0, iter = 0;
     float prev_reg = 0.f;
     auto finish_prev = [&]() {
@@ -581,9 +591,10 @@ __global__ void __launch_bounds__(kCtaThreads, ENG == ENG_CUDA ? 4 : 1) k_cta_ro
     const long long s = *s_budget;
     const float reg = *s_reg;
     // CES: warp w selects the column quads w, w + 8, ... on its own bins.
-    for (int q = warp; q < F / 4; q += kCtaWarps) quad_select<F>(s_x, n, f, s, q, H, tcol, s_P, s_Mk, s_cut);
+    if (!factor_rule)
+        for (int q = warp; q < F / 4; q += kCtaWarps) quad_select<F>(s_x, n, f, s, q, H, tcol, s_P, s_Mk, s_cut);
     __syncthreads();
-    build_masks<F>(s_mask, s_x, n, 0, s_P, s_Mk, s_cut);
+    build_masks<F>(s_mask, s_x, n, 0, s_P, s_Mk, s_cut, factor_rule ? s_idx : nullptr);
     __syncthreads();
     if (masks_out != nullptr)
         for (int e = tid; e < n * W; e += kCtaThreads) masks_out[lo * W + e] = (&s_mask[0][0])[e];
@@ -610,7 +621,7 @@ __global__ void __launch_bounds__(kCtaThreads, ENG == ENG_CUDA ? 4 : 1) k_cta_ro
     if constexpr (TC) {
         if (mode != 2 && blockIdx.x < n_list) {
             finish_prev();
-            tc_pipe_teardown<F, PREC>(P);
+            tc_pipe_teardown<F, PREC>(P, s_bars);
         }
     }
 }
@@ -907,7 +918,11 @@ __global__ void __launch_bounds__(kCtaThreads) k_split_gram(Side side, Params p,
         __syncthreads();
         const ChunkInfo ci = chunk_info<F>(sp, side, c);
         stage_tile<F>(S.x, S.r, S.idx, side, p.f, ci.lo + ci.start, ci.len);
-        build_masks<F>(S.mask, S.x, ci.len, ci.start, st.P + ci.slot * F, st.Mk + ci.slot * F, st.cut + ci.slot * F);
+        if (p.gP != nullptr)  // fast variant: the factor-wide keep rule
+            build_masks<F>(S.mask, S.x, ci.len, ci.start, p.gP, p.gMk, p.gcut, S.idx);
+        else
+            build_masks<F>(S.mask, S.x, ci.len, ci.start, st.P + ci.slot * F, st.Mk + ci.slot * F,
+                           st.cut + ci.slot * F);
         __syncthreads();
         if (masks_out != nullptr)
             for (int e = tid; e < ci.len * W; e += kCtaThreads)
@@ -937,7 +952,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_split_gram(Side side, Params p,
     if constexpr (TC) {
         if (mode != 2 && blockIdx.x < sp.n_chunks) {
             finish_prev();
-            tc_pipe_teardown<F, PREC>(P);
+            tc_pipe_teardown<F, PREC>(P, S.bars);
         }
     }
 }

@@ -197,22 +197,28 @@ __device__ __forceinline__ void tc_pipe_setup(uint8_t* tiles, uint64_t* bars, ui
     P.err = err;
 }
 
+// Wait for the last commit on buffer b. A wait that runs out records the
+// timeout in the error word (the host returns ALS_ERR_TIMEOUT) and clears
+// this thread's ok; the commit stays marked pending so that the teardown can
+// give it one more bounded wait before the tensor memory is freed. Callers
+// make ok uniform across the CTA at their next barrier.
 __device__ __forceinline__ void tc_pipe_drain(TcPipe& P, uint64_t* bars, int b) {
-    if (P.pend[b]) {
-        if (!mbar_wait(&bars[b], P.ph[b])) {
-            // The rows of this CTA from here on store zeros and the host
-            // learns of it from the error word (ALS_ERR_TIMEOUT).
-            if (P.ok) report_timeout(P.err);
+    if (P.pend[b] && P.ok) {
+        if (mbar_wait(&bars[b], P.ph[b])) {
+            P.ph[b] ^= 1u;
+            P.pend[b] = 0;
+        } else {
+            report_timeout(P.err);
             P.ok = false;
         }
-        P.ph[b] ^= 1u;
-        P.pend[b] = 0;
     }
 }
 
 // Accumulate positions [0, n) of a staged tile into accumulator `acc`
 // (0 or 1), starting it from zero when `fresh` (else adding to what it
-// holds). All threads call it; MMAs stay in flight.
+// holds). All threads call it; MMAs stay in flight. Once a wait has run out
+// (ok false, made CTA-uniform at the barrier before the issue) nothing is
+// converted or issued any more.
 template <int F, int PREC, int W>
 __device__ __forceinline__ void tc_pipe_row(TcPipe& P, uint8_t* tiles, uint64_t* bars, const float (*x)[xpitch(F)],
                                             const uint32_t (*mask)[W], const float* r, int n, bool sym, int acc,
@@ -230,7 +236,7 @@ __device__ __forceinline__ void tc_pipe_row(TcPipe& P, uint8_t* tiles, uint64_t*
         uint8_t* B0 = A0 + C::A_BYTES;
         uint8_t* A1 = B0 + C::B_BYTES;
         uint8_t* B1 = A1 + C::A_BYTES;
-        for (int e = tid; e < (F + 1) * GROUPS; e += blockDim.x) {
+        for (int e = tid; P.ok && e < (F + 1) * GROUPS; e += blockDim.x) {
             const int m = e % (F + 1), g = e / (F + 1);
             float va[8], vb[8], la[8], lb[8];
 #pragma unroll
@@ -270,7 +276,8 @@ __device__ __forceinline__ void tc_pipe_row(TcPipe& P, uint8_t* tiles, uint64_t*
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
+        P.ok = __syncthreads_and(P.ok) != 0;
+        if (!P.ok) continue;
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
@@ -311,6 +318,7 @@ __device__ __forceinline__ void tc_pipe_finish(TcPipe& P, uint64_t* bars, int ac
     using C = TcCfg<F, PREC>;
     tc_pipe_drain(P, bars, 0);
     tc_pipe_drain(P, bars, 1);
+    P.ok = __syncthreads_and(P.ok) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;");
     TcCtx ctx;
     ctx.tmem = P.tmem + (uint32_t)acc * C::TMEM_COLS;
@@ -319,9 +327,18 @@ __device__ __forceinline__ void tc_pipe_finish(TcPipe& P, uint64_t* bars, int ac
     tc_store<F, PREC>(ctx, empty, store);
 }
 
+// Free the accumulators. After a wait that ran out, each commit still marked
+// pending gets one more bounded wait first (the MMAs it covers write the
+// tensor memory that is about to be freed).
 template <int F, int PREC>
-__device__ __forceinline__ void tc_pipe_teardown(const TcPipe& P) {
+__device__ __forceinline__ void tc_pipe_teardown(TcPipe& P, uint64_t* bars) {
     using C = TcCfg<F, PREC>;
+    if (!P.ok)
+        for (int b = 0; b < 2; ++b)
+            if (P.pend[b] && mbar_wait(&bars[b], P.ph[b])) {
+                P.ph[b] ^= 1u;
+                P.pend[b] = 0;
+            }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if ((threadIdx.x >> 5) == 0)

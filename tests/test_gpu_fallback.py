@@ -107,7 +107,7 @@ def test_bounded_wait_runs_out_reports_and_handle_stays_usable(core):
     csr, Y = rows_problem([0, 5, 40, 300, 2000], 3000, 64, seed=41)
     eng = core.CoreALS(64, 0.05, 0.25)
     with pytest.raises(B.AlsError) as e:
-        eng._call(eng.lib.als_wait_selftest, 1_000_000)  # 1 ms of GPU time
+        eng._call(eng.lib.als_wait_selftest, 1_000_000, 0)  # 1 ms of GPU time
     assert e.value.status == -5 and B.STATUS[-5] == "ALS_ERR_TIMEOUT"
     # Cleared: the next report is clean, and a half-sweep (tensor-core Gram
     # at n_f = 64) still matches the oracle.
@@ -118,4 +118,24 @@ def test_bounded_wait_runs_out_reports_and_handle_stays_usable(core):
                                  oracle.GRAM_ASYM)
     assert rel_fro(X, Xo) <= 1e-5
     with pytest.raises(B.AlsError):
-        eng._call(eng.lib.als_wait_selftest, -1)
+        eng._call(eng.lib.als_wait_selftest, -1, 0)
+
+
+def test_fit_without_report_still_returns_a_timeout(core):
+    # The record left by a wait that ran out must reach the caller of
+    # als_fit even when no report is asked for; the next fit is clean.
+    import ctypes
+    from paper_2509_18024_gb300 import binding as B
+    p = synth.make_workload("small")
+    Ru = core.DeviceCSR.from_host(p.train_rows)
+    Ri = core.DeviceCSR.from_host(p.train_cols)
+    eng = core.CoreALS(p.f, 0.1, 0.5)
+    M = torch.as_tensor(synth.init_factor(p.n_m, p.f, 1000)).cuda()
+    U = torch.empty((p.n_u, p.f), device="cuda")
+    eng._call(eng.lib.als_wait_selftest, 1_000_000, 1)  # leaves the record
+    args = (ctypes.byref(Ru.c_struct()), ctypes.byref(Ri.c_struct()), 2, B.ptr(U), B.ptr(M), 0, None, None, None,
+            None)
+    with pytest.raises(B.AlsError) as e:
+        eng._call(eng.lib.als_fit, *args)
+    assert e.value.status == -5
+    eng._call(eng.lib.als_fit, *args)

@@ -61,6 +61,11 @@ def parse():
                     help="model width for --workload zipf_1m (default 64) or --capture-case (default 32)")
     ap.add_argument("--capture-case", choices=sorted(synth.CAPTURE_CASES), default=None,
                     help="run one half-sweep of a small single-bucket case three times (for ncu captures)")
+    ap.add_argument("--sketch", choices=["slice", "factor"], default="slice",
+                    help="factor: the fast variant (CES once on the whole design factor)")
+    ap.add_argument("--no-large", action="store_true", help="skip the 10^8-cell n_f = 128 records")
+    ap.add_argument("--no-sim", action="store_true", help="skip the simulation-design metrics")
+    ap.add_argument("--no-probes", action="store_true", help="skip the roofline probes")
     return ap.parse_args()
 
 
@@ -191,7 +196,7 @@ def gpu_arm(args, p, w, M0, r, rank, world, local_rank):
     Ru = core_als.DeviceCSR.from_host(p.train_rows, dev)
     Ri = core_als.DeviceCSR.from_host(p.train_cols, dev)
     tu, tm, tr = (torch.as_tensor(a).to(dev) for a in (p.test_u, p.test_m, p.test_r))
-    eng = core_als.CoreALS(f, lam, r, gram_mode="asym", precision=PRECISIONS[args.precision])
+    eng = core_als.CoreALS(f, lam, r, gram_mode="asym", precision=PRECISIONS[args.precision], sketch=args.sketch)
     M = torch.as_tensor(M0).to(dev)
     U = torch.empty((p.n_u, f), dtype=torch.float32, device=dev)
     tuning = None
@@ -253,7 +258,7 @@ def gpu_arm(args, p, w, M0, r, rank, world, local_rank):
     top = max(fam, key=lambda k: fam[k][0])
     t_top, n_top = fam[top]
     avg_s = t_top / n_top / 1e3
-    roof = roofline(top, avg_s, p, f, r, n_top / prof_steps)
+    roof = roofline(top, avg_s, p, f, r, n_top / prof_steps, getattr(args, "ffma_peak", None))
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -296,7 +301,7 @@ def kernel_sources_hash():
     return h.hexdigest()[:16]
 
 
-def roofline(top, avg_s, p, f, r, launches_per_sweep):
+def roofline(top, avg_s, p, f, r, launches_per_sweep, peak=None):
     """Roofline entry of the dominant kernel family: algorithmic FP32 flops
     of the rows it handles (2 s_i f^2 for X*^T X plus 2 s_i f for X*^T r, with
     s_i = floor(n_i r)), per launch: a sweep's flops over its measured
@@ -323,17 +328,20 @@ def roofline(top, avg_s, p, f, r, launches_per_sweep):
     traffic = None
     if top == TRAFFIC["kernel"] and kernel_sources_hash() == TRAFFIC["sources_sha256_16"]:
         traffic = TRAFFIC["bytes_per_sweep"] / launches_per_sweep
-    return {"bound": "alu", "achieved": achieved, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP32_ALU_PEAK_TFLOPS, "traffic": traffic, "traffic_unit": "bytes per launch",
+    if peak:
+        pk, src = peak, "of measured: ALS_PROBE_FFMA (FP32 FMA throughput probe) in this run"
+    else:
+        pk, src = FP32_ALU_PEAK_TFLOPS, "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"
+    return {"bound": "alu", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+            "frac": achieved / pk, "traffic": traffic, "traffic_unit": "bytes per launch",
             "algorithmic_flops_per_launch": per_launch, "kernel": top,
-            "avg_launch_ms": avg_s * 1e3,
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"}
+            "avg_launch_ms": avg_s * 1e3, "peak_source": src}
 
 
-def e2e_leg(p, w, r, M0, steps=3):
-    """Through the host-buffer C-ABI call (als_fit_host, one sweep per step):
-    every step copies both sides' structure, M^(0) and the test set from
-    pinned host memory and reads U and M back."""
+def e2e_leg(p, w, r, M0, steps=3, sweeps=1):
+    """Through the host-buffer C-ABI call (als_fit_host, `sweeps` sweeps per
+    step): every step copies both sides' structure, M^(0) and the test set
+    from pinned host memory and reads U and M back."""
     import torch
     from paper_2509_18024_gb300 import core_als
 
@@ -348,16 +356,17 @@ def e2e_leg(p, w, r, M0, steps=3):
     test = (pinned(p.test_u), pinned(p.test_m), pinned(p.test_r))
     M0p = pinned(M0)
     eng = core_als.CoreALS(w["f"], w["lam"], r)
-    eng.fit_host(rows, cols, M0p, 1, test=test)  # warm
+    eng.fit_host(rows, cols, M0p, sweeps, test=test)  # warm
     t0 = time.perf_counter()
     for _ in range(steps):
-        eng.fit_host(rows, cols, M0p, 1, test=test)
+        eng.fit_host(rows, cols, M0p, sweeps, test=test)
     dt = time.perf_counter() - t0
     nnz, f = p.train_rows.nnz, w["f"]
     h2d = (p.n_u + 1) * 8 + (p.n_m + 1) * 8 + 2 * nnz * 8 + p.n_m * f * 4 + len(p.test_r) * 12
     d2h = (p.n_u + p.n_m) * f * 4
-    return {"value": (p.n_u + p.n_m) * steps / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "api": "als_fit_host (1 sweep per call, incl. validation)"}
+    return {"value": (p.n_u + p.n_m) * steps * sweeps / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h),
+            "api": f"als_fit_host ({sweeps} sweep{'s' if sweeps > 1 else ''} per call, incl. validation)"}
 
 
 PRECISIONS = {"fp32": 0, "tf32": 1, "bf16": 2, "fp32_tc": 3}
@@ -370,8 +379,8 @@ def variants(p, w, M0, rvals, steps=5):
     Ru = core_als.DeviceCSR.from_host(p.train_rows)
     Ri = core_als.DeviceCSR.from_host(p.train_cols)
     out = {}
-    for name, r, mode, prec in rvals:
-        eng = core_als.CoreALS(w["f"], w["lam"], r, gram_mode=mode, precision=PRECISIONS[prec])
+    for name, r, mode, prec, *kw in rvals:
+        eng = core_als.CoreALS(w["f"], w["lam"], r, gram_mode=mode, precision=PRECISIONS[prec], **(kw[0] if kw else {}))
         M = torch.as_tensor(M0).cuda()
         U = torch.empty((p.n_u, w["f"]), dtype=torch.float32, device="cuda")
         for _ in range(2):
@@ -401,8 +410,8 @@ def time_to_rmse(p, w, M0, settings, sweeps=15):
     Ri = core_als.DeviceCSR.from_host(p.train_cols)
     tu, tm, tr = (torch.as_tensor(a).cuda() for a in (p.test_u, p.test_m, p.test_r))
     curves = {}
-    for name, r, mode, prec in settings:
-        eng = core_als.CoreALS(w["f"], w["lam"], r, gram_mode=mode, precision=PRECISIONS[prec])
+    for name, r, mode, prec, *kw in settings:
+        eng = core_als.CoreALS(w["f"], w["lam"], r, gram_mode=mode, precision=PRECISIONS[prec], **(kw[0] if kw else {}))
         eng.prepare(Ru)
         eng.prepare(Ri)
         M = torch.as_tensor(M0).cuda()
@@ -429,43 +438,36 @@ def time_to_rmse(p, w, M0, settings, sweeps=15):
     return res
 
 
-def large_arm(args):
-    """--workload zipf_1m: sweep throughput at n_f = 64 / 128 on the
-    10^8-cell matrix (drawn on the device), the error of one user half-sweep
-    against the FP64 oracle on 10,000 sampled rows, and the oracle's own rate
-    on that sample."""
+def large_leg(d, w, f, precision, steps, warmup, seed, sample_rows=10000, clocks=True):
+    """Sweep throughput on the 1M x 100k, 10^8-cell matrix (drawn on the
+    device) at width f: ms per sweep (CUDA events, L2 flushed between
+    sweeps), per-kernel times from one separately profiled sweep, and the
+    error of one user half-sweep from M^(0) against the FP64 oracle on
+    `sample_rows` sampled rows, with the oracle's own rate on that sample."""
     import torch
     import oracle
     from paper_2509_18024_gb300 import core_als
-    w = dict(synth.WORKLOADS["zipf_1m"])
-    f, lam = args.nf or 64, w["lam"]
-    r = args.budget if args.budget is not None else w["budget"]
-    t0 = time.perf_counter()
-    d = synth.zipf_ratings_device(w["n_u"], w["n_m"], w["f"], w["nnz"], w["zipf_s"], w["noise_sd"], args.seed)
-    torch.cuda.synchronize()
-    gen_s = time.perf_counter() - t0
+    lam = w["lam"]
+    r = w["budget"]
     Ru = core_als.DeviceCSR(w["n_u"], w["n_m"], *d.rows)
     Ri = core_als.DeviceCSR(w["n_m"], w["n_u"], *d.cols)
     M0 = synth.init_factor(w["n_m"], f, 1000)
-    eng = core_als.CoreALS(f, lam, r, precision=PRECISIONS[args.precision])
+    eng = core_als.CoreALS(f, lam, r, precision=PRECISIONS[precision])
     M = torch.as_tensor(M0).cuda()
     U = torch.empty((w["n_u"], f), dtype=torch.float32, device="cuda")
-    # Error of one half-sweep from M^(0) against the FP64 oracle on a sample.
     eng.half_sweep(Ru, M, U)
-    rng = np.random.default_rng(args.seed)
-    rows = np.sort(rng.choice(w["n_u"], size=10000, replace=False))
+    rng = np.random.default_rng(seed)
+    rows = np.sort(rng.choice(w["n_u"], size=sample_rows, replace=False))
     indptr, indices, values = (t.cpu().numpy() for t in d.rows)
     t1 = time.perf_counter()
-    Xo, _, _ = oracle.half_sweep(indptr, indices, values, M0.astype(np.float64), lam, r, oracle.GRAM_ASYM,
-                                 rows=rows)
+    Xo, _, _ = oracle.half_sweep(indptr, indices, values, M0.astype(np.float64), lam, r, oracle.GRAM_ASYM, rows=rows)
     t_or = time.perf_counter() - t1
     Xg = U.cpu().numpy()[rows].astype(np.float64)
     Xo = Xo[rows]
     err = float(np.linalg.norm(Xg - Xo) / np.linalg.norm(Xo))
     row_err = np.linalg.norm(Xg - Xo, axis=1) / np.maximum(np.linalg.norm(Xo, axis=1), 1e-300)
     L = np.diff(indptr)
-    or_rate = w["n_u"] * 1.0 / (t_or * Ru.nnz / max(int(L[rows].sum()), 1))  # user rows/s, by entries
-    # Throughput.
+    or_rate = w["n_u"] * 1.0 / (t_or * Ru.nnz / max(int(L[rows].sum()), 1))
     sse = torch.zeros(1, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
@@ -474,49 +476,133 @@ def large_arm(args):
         eng.half_sweep(Ri, U, M)
         eng.sse_async(d.test_u, d.test_m, d.test_r, U, M, sse)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     launches0 = eng.launch_count
-    with ClockSampler(0) as clk:
-        for q in range(args.steps):
-            flush.zero_()
-            evs[q][0].record(stream)
-            step()
-            evs[q][1].record(stream)
-        torch.cuda.synchronize()
+    clk = ClockSampler(0) if clocks else None
+    if clk:
+        clk.__enter__()
+    for q in range(steps):
+        flush.zero_()
+        evs[q][0].record(stream)
+        step()
+        evs[q][1].record(stream)
+    torch.cuda.synchronize()
+    if clk:
+        clk.__exit__(None, None, None)
     ms = sum(a.elapsed_time(b) for a, b in evs)
     launches = eng.launch_count - launches0
-    # Per-kernel times: one separate profiled step (each launch alone on the stream).
-    prof_steps = 1
     eng.profile(True)
     flush.zero_()
     step()
     torch.cuda.synchronize()
-    fam = {k: eng.kernel_time(k) for k in KERNEL_FAMILIES + ("refine_resid", "fp64_rows", "add_rows")}
+    fam = {k: eng.kernel_time(k) for k in KERNEL_FAMILIES + ("refine_resid", "fp64_rows", "add_rows", "colmax")}
     fam = {k: v for k, v in fam.items() if v[1]}
     eng.profile(False)
+    eng.close()
+    total = sum(v[0] for v in fam.values()) or 1.0
     n_rows = w["n_u"] + w["n_m"]
-    out = {"metric": METRIC, "value": n_rows * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic (device-drawn Zipf)",
+    return {"n_f": f, "precision": precision, "refine_steps": "auto", "ms_per_sweep": ms / steps,
+            "row_solves_per_s": n_rows * steps / (ms / 1e3), "gpu_launches_per_sweep": launches / steps,
+            "clocks": clk.summary() if clk else None,
+            "kernel_ms_per_sweep": {k: v[0] for k, v in fam.items()},
+            "kernel_share": {k: v[0] / total for k, v in fam.items()},
+            "kernels_timing": "one separate profiled sweep, each launch alone on the stream",
+            "error_vs_fp64_oracle": {"sample_rows": len(rows), "rel_fro": err, "row_rel_max": float(row_err.max()),
+                                     "row_rel_p99": float(np.quantile(row_err, 0.99)),
+                                     "what": "one user half-sweep from the same M^(0)"},
+            "oracle_user_rows_per_s": or_rate, "oracle_cores": oracle.num_threads(),
+            "test_rmse_after_timed_sweeps": float(np.sqrt(sse.item() / d.test_r.numel()))}
+
+
+def draw_large(seed):
+    import torch
+    w = dict(synth.WORKLOADS["zipf_1m"])
+    t0 = time.perf_counter()
+    d = synth.zipf_ratings_device(w["n_u"], w["n_m"], w["f"], w["nnz"], w["zipf_s"], w["noise_sd"], seed)
+    torch.cuda.synchronize()
+    return d, w, time.perf_counter() - t0
+
+
+def large_arm(args):
+    """--workload zipf_1m: the 10^8-cell matrix at --nf (default 64) and
+    --precision, as one JSON line."""
+    d, w, gen_s = draw_large(args.seed)
+    f = args.nf or 64
+    if args.budget is not None:
+        w["budget"] = args.budget
+    res = large_leg(d, w, f, args.precision, args.steps, args.warmup, args.seed)
+    out = {"metric": METRIC, "value": res["row_solves_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": res["ms_per_sweep"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": args.precision, "data": "synthetic (device-drawn Zipf)",
            "config": {"workload": f"zipf_1m: {w['n_u']} users x {w['n_m']} items, {w['nnz']} cells (Zipf "
-                                  f"{w['zipf_s']}), n_f={f}, lambda={lam}, r={r}, asymmetric Eq. core_ui",
-                      "n_f": f, "precision": args.precision, "refine_steps": "auto",
-                      "l2": "flushed between steps (256 MB write)", "generation_s": round(gen_s, 1)},
-           "gpu_launches": launches, "clocks": clk.summary(),
-           "kernels_ms_per_step": {k: v[0] / prof_steps for k, v in fam.items()},
-           "kernels_timing": "one separate profiled step, each launch alone on the stream",
-           "error_vs_fp64_oracle": {"sample_rows": len(rows), "rel_fro": err, "row_rel_max": float(row_err.max()),
-                                    "row_rel_p99": float(np.quantile(row_err, 0.99)),
-                                    "what": "one user half-sweep from the same M^(0)"},
-           "cpu_baseline": {"value": or_rate, "unit": "user row-solves/s", "cores": oracle.num_threads(),
-                            "kind": "oracle", "sample": f"{len(rows)} random user rows, one half-sweep, "
-                                                       f"extrapolated by observed entries"},
-           "test_rmse_after_timed_sweeps": float(np.sqrt(sse.item() / d.test_r.numel()))}
+                                  f"{w['zipf_s']}), n_f={f}, lambda={w['lam']}, r={w['budget']}, asymmetric Eq. core_ui",
+                      "n_f": f, "precision": args.precision, "l2": "flushed between steps (256 MB write)",
+                      "generation_s": round(gen_s, 1)},
+           "gpu_launches": res["gpu_launches_per_sweep"] * args.steps, "clocks": res["clocks"],
+           "kernels_ms_per_step": res["kernel_ms_per_sweep"], "kernels_timing": res["kernels_timing"],
+           "error_vs_fp64_oracle": res["error_vs_fp64_oracle"],
+           "cpu_baseline": {"value": res["oracle_user_rows_per_s"], "unit": "user row-solves/s",
+                            "cores": res["oracle_cores"], "kind": "oracle",
+                            "sample": "10000 random user rows, one half-sweep, extrapolated by observed entries"},
+           "test_rmse_after_timed_sweeps": res["test_rmse_after_timed_sweeps"]}
     print(json.dumps(out), flush=True)
+
+
+def simulation_leg(seed=1, sweeps=10, r=0.2):
+    """The simulation design of Sec. 5.1 (3600 x 3600, n_f = 60, D1 factors
+    with 0.6^|i-j| covariance, N(0,1) noise, 40 % of cells removed - R1):
+    CORE (Algorithm 2), its fast variant and FULL ALS from the same M^(0),
+    with ReMSE on the empirical set, P-ReMSE on the prediction set, and
+    Hit@5 / NDCG@10 against the prediction-set items whose value is in the
+    top 5 % (all computed by the library's kernels), and sweep times."""
+    import torch
+    from paper_2509_18024_gb300 import core_als
+    p = synth.simulation("D1", synth.SIM_MISSING["R1"], seed=seed)
+    Ru = core_als.DeviceCSR.from_host(p.train_rows)
+    Ri = core_als.DeviceCSR.from_host(p.train_cols)
+    rows = np.repeat(np.arange(p.n_u, dtype=np.int32), np.diff(p.train_rows.indptr))
+    emp = tuple(torch.as_tensor(np.ascontiguousarray(a)).cuda()
+                for a in (rows, p.train_rows.indices, p.train_rows.values))
+    pred = tuple(torch.as_tensor(np.ascontiguousarray(a)).cuda() for a in (p.pred_u, p.pred_m, p.pred_r))
+    rel = core_als.DeviceCSR.from_host(synth.relevant_items(p.n_u, p.n_m, p.pred_u, p.pred_m, p.pred_r,
+                                                            synth.top_share_threshold(p.pred_r, 0.05)))
+    M0 = torch.as_tensor(synth.init_factor(p.n_m, p.f, 77)).cuda()
+    out = {"design": "Sec. 5.1: 3600 x 3600, n_f = 60, D1 N(0, 0.6^|i-j|) factors, N(0,1) noise, R1 (40 % removed)",
+           "lambda": 0.01, "budget": r, "sweeps": sweeps}
+    for name, kw in (("core", dict()), ("core_fast", dict(sketch="factor")), ("full", dict(gram_mode="full"))):
+        eng = core_als.CoreALS(p.f, 0.01, 1.0 if name == "full" else r, **kw)
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            U, M, rep = eng.fit(Ru, Ri, M0, 1)  # plans, workspace
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            U, M, rep = eng.fit(Ru, Ri, M0, sweeps)
+            b.record()
+        s.synchronize()
+        hit, ndcg, n_eval = eng.ranking(Ru, rel, U, M, 5, 10)
+        out[name] = {"ReMSE": eng.remse(*emp, U, M), "P-ReMSE": eng.remse(*pred, U, M), "Hit@5": hit,
+                     "NDCG@10": ndcg, "users_evaluated": n_eval, "objective": rep["objective"],
+                     "ms_per_sweep": a.elapsed_time(b) / sweeps}
+        eng.close()
+    return out
+
+
+def peaks_leg():
+    """Project-written roofline probes (als_probe), each one timed launch."""
+    from paper_2509_18024_gb300 import core_als
+    out = {}
+    for kind, key in (("ffma", "fp32_ffma_tflops"), ("dfma", "fp64_dfma_tflops"), ("tc_bf16", "tc_bf16_tflops"),
+                      ("tc_tf32", "tc_tf32_tflops"), ("l2_gather", "l2_gather_gbs"), ("hbm_copy", "hbm_copy_gbs")):
+        try:
+            out[key] = core_als.probe(kind)[0]
+        except Exception as e:  # a probe that cannot run on this device
+            out[key] = None
+            out[key + "_error"] = str(e)
+    return out
 
 
 def warmstart_arm(args):
@@ -694,19 +780,37 @@ def main():
         dist.init_process_group("nccl")
     p = synth.make_workload(WORKLOAD, seed=args.seed)
     M0 = synth.init_factor(p.n_m, p.f, 1000)
+    peaks = None
+    if rank == 0 and not args.no_probes:
+        import torch
+        torch.cuda.set_device(local_rank)
+        peaks = peaks_leg()
+        args.ffma_peak = peaks.get("fp32_ffma_tflops")
     res = gpu_arm(args, p, w, M0, r, rank, world, local_rank)
     if rank == 0:
         out, eng, _, _ = res
+        if peaks is not None:
+            out["peaks_measured"] = peaks
+            if os.path.exists(PEAKS_FILE):
+                with open(PEAKS_FILE) as fh:
+                    out["peaks_measured"]["driver_measured_peaks_file"] = json.load(fh)
         out["e2e"] = e2e_leg(p, w, r, M0)
+        out["e2e_fit_15_sweeps"] = e2e_leg(p, w, r, M0, steps=2, sweeps=15)
         if not args.no_variants:
             out["variants_rows_per_s"] = variants(p, w, M0, [
                 ("full_als_fp32", 1.0, "full", "fp32"), ("core_r0.10_fp32", 0.10, "asym", "fp32"),
                 ("core_r0.50_fp32", 0.50, "asym", "fp32"), ("core_r0.25_fp32_tc", r, "asym", "fp32_tc"),
                 ("core_r0.25_tf32", r, "asym", "tf32"), ("core_r0.25_bf16", r, "asym", "bf16"),
-                ("full_als_bf16", 1.0, "full", "bf16")])
+                ("full_als_bf16", 1.0, "full", "bf16"),
+                ("core_fast_r0.25_fp32", r, "asym", "fp32", {"sketch": "factor"}),
+                ("core_fast_r0.25_bf16", r, "asym", "bf16", {"sketch": "factor"}),
+                ("core_fixed_s8_fp32", r, "asym", "fp32", {"fixed_keep": 8}),
+                ("core_fixed_s32_fp32", r, "asym", "fp32", {"fixed_keep": 32})])
             out["time_to_rmse"] = time_to_rmse(p, w, M0, [
                 ("core_fp32", r, "asym", "fp32"), ("core_tf32", r, "asym", "tf32"), ("core_bf16", r, "asym", "bf16"),
-                ("core_fp32_tc", r, "asym", "fp32_tc"), ("full_fp32", 1.0, "full", "fp32")])
+                ("core_fp32_tc", r, "asym", "fp32_tc"), ("full_fp32", 1.0, "full", "fp32"),
+                ("core_fast_fp32", r, "asym", "fp32", {"sketch": "factor"}),
+                ("core_fixed_s32_fp32", r, "asym", "fp32", {"fixed_keep": 32})])
         if world == 1 and not args.no_cpu_baseline:
             rate, done, t_sweep = oracle_sample(p, M0, w["lam"], r, 40000, 8000, 7)
             import oracle
@@ -714,6 +818,21 @@ def main():
                                    "sample": f"{done} random rows (40000 user + 8000 item rows), one half-sweep "
                                              f"each, extrapolated to a full sweep by observed entries "
                                              f"(est. {t_sweep:.1f} s per sweep)"}
+        if world == 1 and not args.no_sim:
+            out["simulation_metrics"] = simulation_leg()
+        if world == 1 and not args.no_large:
+            import torch
+            eng.close()
+            torch.cuda.empty_cache()
+            d, wl, gen_s = draw_large(args.seed)
+            out["zipf_1m_nf128"] = {"workload": f"zipf_1m: {wl['n_u']} users x {wl['n_m']} items, {wl['nnz']} cells "
+                                                f"(Zipf {wl['zipf_s']}), n_f=128, lambda={wl['lam']}, "
+                                                f"r={wl['budget']}, asymmetric Eq. core_ui; 2 timed sweeps each",
+                                    "generation_s": round(gen_s, 1)}
+            for prec in ("fp32", "bf16"):
+                out["zipf_1m_nf128"][prec] = large_leg(d, wl, 128, prec, steps=2, warmup=1, seed=args.seed)
+                torch.cuda.empty_cache()
+            del d
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -427,6 +427,29 @@ int als_mlp_grad(als_mlp* m, int64_t n, const float* X, const float* T, float* g
  * loss before the step (synchronises only when given). */
 int als_mlp_train_step(als_mlp* m, int64_t n, const float* X, const float* T, float lr, double* loss_host);
 
+/* ---------------------------------------------------------------------------
+ * Roofline probes (no counterpart in the paper: the measured peaks that the
+ * kernels' roofline fractions are taken against). Each allocates and frees
+ * its own buffers, runs one warm-up and one timed launch on cuda_stream
+ * (a cudaStream_t, NULL = legacy default stream), synchronises, and writes
+ * the achieved rate to value_host (TFLOP/s, or GB/s for the two memory
+ * probes) and the timed launch's CUDA-event duration to ms_host (nullable):
+ *   ALS_PROBE_FFMA       FP32 FMA, 8 independent chains per thread
+ *   ALS_PROBE_DFMA       FP64 FMA, the same shape
+ *   ALS_PROBE_TC_BF16    tcgen05.mma kind::f16 (BF16), M 128 x N 256, one CTA
+ *                        per SM, operands in shared memory, accumulator in TMEM
+ *   ALS_PROBE_TC_TF32    the same with kind::tf32
+ *   ALS_PROBE_L2_GATHER  random 128-byte row gathers from a 16 MB factor
+ *   ALS_PROBE_HBM_COPY   a 2 GB device-to-device copy kernel (read + write)
+ * ALS_ERR_TIMEOUT when a tensor-core probe's bounded wait ran out. */
+#define ALS_PROBE_FFMA 0
+#define ALS_PROBE_DFMA 1
+#define ALS_PROBE_TC_BF16 2
+#define ALS_PROBE_TC_TF32 3
+#define ALS_PROBE_L2_GATHER 4
+#define ALS_PROBE_HBM_COPY 5
+int als_probe(int kind, double* value_host, double* ms_host, void* cuda_stream);
+
 /* Bytes of device workspace the handle currently holds. */
 int64_t als_workspace_bytes(const als_handle* h);
 

@@ -24,6 +24,7 @@ ALS_FP32, ALS_TF32, ALS_BF16, ALS_FP32_TC = 0, 1, 2, 3
 ALS_FLAG_RATIO, ALS_FLAG_SINGULAR, ALS_FLAG_FP64 = 1, 2, 4
 ALS_REFINE_AUTO = -1
 ALS_SKETCH_SLICE, ALS_SKETCH_FACTOR = 0, 1
+PROBES = {"ffma": 0, "dfma": 1, "tc_bf16": 2, "tc_tf32": 3, "l2_gather": 4, "hbm_copy": 5}
 ALS_SSE_STATIC_MAX_ENTRIES = 4096 * 16384
 
 
@@ -105,6 +106,7 @@ SIGNATURES = {
     "als_mlp_forward": (C.c_int, [_P, _I64, _P, _P]),
     "als_mlp_grad": (C.c_int, [_P, _I64, _P, _P, _P, _P]),
     "als_mlp_train_step": (C.c_int, [_P, _I64, _P, _P, C.c_float, _P]),
+    "als_probe": (C.c_int, [C.c_int, _P, _P, _P]),
     "als_workspace_bytes": (_I64, [_P]),
     "als_launch_count": (_I64, [_P]),
     "als_status_string": (C.c_char_p, [C.c_int]),

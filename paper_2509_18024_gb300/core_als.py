@@ -320,6 +320,17 @@ class CoreBatch:
             pass
 
 
+def probe(kind: str):
+    """(rate, ms) of one roofline probe (als_probe): TFLOP/s for ffma, dfma,
+    tc_bf16, tc_tf32; GB/s for l2_gather and hbm_copy."""
+    _require_cuda()
+    lib = B.load()
+    v, ms = C.c_double(), C.c_double()
+    B.check(lib.als_probe(B.PROBES[kind], C.byref(v), C.byref(ms),
+                          C.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    return v.value, ms.value
+
+
 def features(R: DeviceCSR, Y: torch.Tensor, n_f: int) -> torch.Tensor:
     """Per-row warm-start features of one side (n_rows x (n_f + 2))."""
     lib = B.load()

@@ -102,7 +102,7 @@ __device__ __forceinline__ void report_timeout(unsigned* err) {
 // Self-test of the bounded wait: thread 0 waits on a fresh barrier that
 // nothing arrives at, so the wait runs out after limit_ns and is recorded in
 // the error word exactly as a timeout of the tensor-core pipelines is.
-__global__ void k_wait_selftest(uint64_t limit_ns, unsigned* err) {
+static __global__ void k_wait_selftest(uint64_t limit_ns, unsigned* err) {
     __shared__ __align__(8) uint64_t bar;
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar)));

@@ -478,6 +478,76 @@ __device__ __forceinline__ void quad_select(const float (*x)[xpitch(F)], int n, 
 }
 
 // ---------------------------------------------------------------------------
+// Sparse asymmetric Gram of one warp's four columns a = 4q .. 4q+3 of a staged
+// slice (F = 32): row a of X*^T X is sum over the kept positions k of column
+// a of x_ka X[k][:], and the rhs entry sum_k x_ka r_k, so only the s kept
+// positions are visited (2 s F^2 flops for the row, Theorem 4's count).
+// The warp lists each column's kept positions (keep rule P, Mk, cut of its
+// selection) in `list` (4 x lcap uint16), ORs the columns' keep bits into the
+// CTA's mask words when `mask` is given, and writes the four rows of the
+// augmented system [G | b] (regulariser on the diagonal, padding rows
+// identity) to dst. Lanes: group g = lane / 8 takes row a = 4q + g, lane
+// j = lane % 8 its columns 4j .. 4j+3.
+template <int F>
+__device__ __forceinline__ void sparse_gram_rows(const float (*x)[xpitch(F)], const float* r, int n, int f, float reg,
+                                                 int q, const uint32_t* P, const uint32_t* Mk, const int32_t* cut,
+                                                 uint16_t* list, int lcap, uint32_t* mask, float* dst) {
+    static_assert(F == 32, "four columns per warp, eight lanes per row");
+    const int lane = threadIdx.x & 31;
+    uint32_t Pc[4], Mc[4];
+    int Cc[4], cnt[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        Pc[c] = P[4 * q + c];
+        Mc[c] = Mk[4 * q + c];
+        Cc[c] = cut[4 * q + c];
+    }
+    const unsigned below = lanemask_lt();
+    for (int kb = 0; kb < n; kb += 32) {
+        const int k = kb + lane;
+        uint32_t nib = 0u;
+        if (k < n) {
+            const float4 v = reinterpret_cast<const float4*>(x[k])[q];
+            nib = (uint32_t)keep_rule(mag_key(v.x), Pc[0], Mc[0], k, Cc[0]) |
+                  ((uint32_t)keep_rule(mag_key(v.y), Pc[1], Mc[1], k, Cc[1]) << 1) |
+                  ((uint32_t)keep_rule(mag_key(v.z), Pc[2], Mc[2], k, Cc[2]) << 2) |
+                  ((uint32_t)keep_rule(mag_key(v.w), Pc[3], Mc[3], k, Cc[3]) << 3);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const unsigned b = __ballot_sync(kFull, (nib >> c) & 1u);
+            const int at = cnt[c] + __popc(b & below);
+            if (((nib >> c) & 1u) && at < lcap) list[c * lcap + at] = (uint16_t)k;
+            cnt[c] += __popc(b);
+        }
+        if (mask != nullptr && nib) atomicOr(mask + k, nib << (4 * q));
+    }
+    __syncwarp();
+    const int g = lane >> 3, j = lane & 7, a = 4 * q + g;
+    const int na = min(g == 0 ? cnt[0] : g == 1 ? cnt[1] : g == 2 ? cnt[2] : cnt[3], lcap);
+    const uint16_t* la = list + g * lcap;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, rh = 0.f;
+    for (int t = 0; t < na; ++t) {
+        const int k = la[t];
+        const float xa = x[k][a];
+        const float4 xb = reinterpret_cast<const float4*>(x[k])[j];
+        a0 = fmaf(xa, xb.x, a0);
+        a1 = fmaf(xa, xb.y, a1);
+        a2 = fmaf(xa, xb.z, a2);
+        a3 = fmaf(xa, xb.w, a3);
+        rh = fmaf(xa, r[k], rh);
+    }
+    float* row = dst + a * (F + 1);
+    const float v[4] = {a0, a1, a2, a3};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int c = 4 * j + e;
+        row[c] = (a == c) ? ((a < f) ? v[e] + reg : 1.f) : v[e];
+    }
+    if (j == 0) row[F] = rh;
+}
+
+// ---------------------------------------------------------------------------
 // CTA per row, slice resident in shared memory.
 // Bytes of the two tensor-core tile buffers of an engine (16 for CUDA cores).
 template <int F, int ENG>
@@ -511,7 +581,14 @@ struct CtaLayout {
     __host__ __device__ static constexpr size_t r(int cap) { return x + x_bytes(cap); }
     __host__ __device__ static constexpr size_t idx(int cap) { return r(cap) + (size_t)cap * 4; }
     __host__ __device__ static constexpr size_t mask(int cap) { return idx(cap) + (size_t)cap * 4; }
-    __host__ __device__ static constexpr size_t bytes(int cap) { return up16(mask(cap) + (size_t)cap * W * 4); }
+    // Kept-position lists of the sparse asymmetric Gram (CUDA cores, F = 32):
+    // per warp 4 columns x cap / 4 positions (uint16).
+    static constexpr bool SPARSE = ENG == ENG_CUDA && F == 32;
+    __host__ __device__ static constexpr int list_cap(int cap) { return cap / 4; }
+    __host__ __device__ static constexpr size_t list(int cap) { return up16(mask(cap) + (size_t)cap * W * 4); }
+    __host__ __device__ static constexpr size_t bytes(int cap) {
+        return up16(list(cap) + (SPARSE ? (size_t)kCtaWarps * 4 * list_cap(cap) * 2 : 0));
+    }
 };
 
 // mode 0/1: write the augmented system of list entry w to G_aug[w]; mode 2:
@@ -541,6 +618,7 @@ __global__ void __launch_bounds__(kCtaThreads, ENG == ENG_CUDA ? 4 : 1) k_cta_ro
     float* const s_r = reinterpret_cast<float*>(smem_raw + L::r(cap));
     int32_t* const s_idx = reinterpret_cast<int32_t*>(smem_raw + L::idx(cap));
     uint32_t (*const s_mask)[W] = reinterpret_cast<uint32_t (*)[W]>(smem_raw + L::mask(cap));
+    uint16_t* const s_list = reinterpret_cast<uint16_t*>(smem_raw + L::list(cap));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int f = p.f;
     constexpr bool TC = ENG != ENG_CUDA;
@@ -587,12 +665,37 @@ __global__ void __launch_bounds__(kCtaThreads, ENG == ENG_CUDA ? 4 : 1) k_cta_ro
         *s_budget = row_budget(n, p);
         *s_reg = row_reg(n, p);
     }
+    // Sparse asymmetric Gram (CUDA cores, F = 32, Algorithm 2's exact budget
+    // s per column, s <= cap / 4): the warp that selected columns 4w..4w+3
+    // lists their kept positions and assembles rows 4w..4w+3 of X*^T X, with
+    // no CTA barrier between selection and Gram. The choice depends on the
+    // row's budget only, so every thread takes the same branch. Its mask
+    // words start at zero (the warps OR their columns' bits into them).
+    if constexpr (L::SPARSE)
+        if (masks_out != nullptr)
+            for (int e = tid; e < n * W; e += kCtaThreads) (&s_mask[0][0])[e] = 0u;
     stage_tile<F>(s_x, s_r, s_idx, side, f, lo, n);
     const long long s = *s_budget;
     const float reg = *s_reg;
+    bool sparse = false;
+    if constexpr (L::SPARSE)
+        sparse = mode != 2 && p.gram_mode == GRAM_ASYM && !factor_rule && s <= (long long)L::list_cap(cap);
     // CES: warp w selects the column quads w, w + 8, ... on its own bins.
     if (!factor_rule)
         for (int q = warp; q < F / 4; q += kCtaWarps) quad_select<F>(s_x, n, f, s, q, H, tcol, s_P, s_Mk, s_cut);
+    if constexpr (L::SPARSE) {
+        if (sparse) {
+            __syncwarp();
+            sparse_gram_rows<F>(s_x, s_r, n, f, reg, warp, s_P, s_Mk, s_cut, s_list + warp * 4 * L::list_cap(cap),
+                                L::list_cap(cap), masks_out != nullptr ? &s_mask[0][0] : nullptr,
+                                G_aug + (int64_t)w * F * (F + 1));
+            if (masks_out != nullptr) {
+                __syncthreads();
+                for (int e = tid; e < n * W; e += kCtaThreads) masks_out[lo * W + e] = (&s_mask[0][0])[e];
+            }
+            continue;
+        }
+    }
     __syncthreads();
     build_masks<F>(s_mask, s_x, n, 0, s_P, s_Mk, s_cut, factor_rule ? s_idx : nullptr);
     __syncthreads();

@@ -478,20 +478,28 @@ __device__ __forceinline__ void quad_select(const float (*x)[xpitch(F)], int n, 
 }
 
 // ---------------------------------------------------------------------------
-// Sparse asymmetric Gram of one warp's four columns a = 4q .. 4q+3 of a staged
-// slice (F = 32): row a of X*^T X is sum over the kept positions k of column
-// a of x_ka X[k][:], and the rhs entry sum_k x_ka r_k, so only the s kept
-// positions are visited (2 s F^2 flops for the row, Theorem 4's count).
-// The warp lists each column's kept positions (keep rule P, Mk, cut of its
-// selection) in `list` (4 x lcap uint16), ORs the columns' keep bits into the
-// CTA's mask words when `mask` is given, and writes the four rows of the
-// augmented system [G | b] (regulariser on the diagonal, padding rows
-// identity) to dst. Lanes: group g = lane / 8 takes row a = 4q + g, lane
-// j = lane % 8 its columns 4j .. 4j+3.
+// Sparse asymmetric Gram (F = 32): row a of X*^T X is the sum over the kept
+// positions k of column a of x_ka X[k][:], and the rhs entry sum_k x_ka r_k,
+// so only the kept positions are visited (2 s F^2 flops for a row with s
+// kept per column, the count of Theorem 4). A warp owns four columns
+// a = 4q .. 4q+3: it lists each column's kept positions of a staged tile
+// (keep rule P, Mk, cut of the selection) and accumulates those four rows in
+// registers - lane group g = lane / 8 takes row a = 4q + g, lane j = lane % 8
+// its columns 4j .. 4j+3.
+struct SparseAcc {
+    float a0, a1, a2, a3, rh;
+    __device__ __forceinline__ void zero() { a0 = a1 = a2 = a3 = rh = 0.f; }
+};
+
+// Lists the kept positions of columns 4q..4q+3 among tile rows [0, n) (tile
+// row k has position pos0 + k in its row, or gpos[k] with the fast variant's
+// factor-wide rule) into list (4 x lcap uint16), ORs their keep bits into
+// mask[k] when mask is given, and returns the number listed for this lane's
+// column.
 template <int F>
-__device__ __forceinline__ void sparse_gram_rows(const float (*x)[xpitch(F)], const float* r, int n, int f, float reg,
-                                                 int q, const uint32_t* P, const uint32_t* Mk, const int32_t* cut,
-                                                 uint16_t* list, int lcap, uint32_t* mask, float* dst) {
+__device__ __forceinline__ int sparse_list(const float (*x)[xpitch(F)], int n, int pos0, const int32_t* gpos, int q,
+                                           const uint32_t* P, const uint32_t* Mk, const int32_t* cut, uint16_t* list,
+                                           int lcap, uint32_t* mask) {
     static_assert(F == 32, "four columns per warp, eight lanes per row");
     const int lane = threadIdx.x & 31;
     uint32_t Pc[4], Mc[4];
@@ -508,10 +516,11 @@ __device__ __forceinline__ void sparse_gram_rows(const float (*x)[xpitch(F)], co
         uint32_t nib = 0u;
         if (k < n) {
             const float4 v = reinterpret_cast<const float4*>(x[k])[q];
-            nib = (uint32_t)keep_rule(mag_key(v.x), Pc[0], Mc[0], k, Cc[0]) |
-                  ((uint32_t)keep_rule(mag_key(v.y), Pc[1], Mc[1], k, Cc[1]) << 1) |
-                  ((uint32_t)keep_rule(mag_key(v.z), Pc[2], Mc[2], k, Cc[2]) << 2) |
-                  ((uint32_t)keep_rule(mag_key(v.w), Pc[3], Mc[3], k, Cc[3]) << 3);
+            const int pos = gpos ? gpos[k] : pos0 + k;
+            nib = (uint32_t)keep_rule(mag_key(v.x), Pc[0], Mc[0], pos, Cc[0]) |
+                  ((uint32_t)keep_rule(mag_key(v.y), Pc[1], Mc[1], pos, Cc[1]) << 1) |
+                  ((uint32_t)keep_rule(mag_key(v.z), Pc[2], Mc[2], pos, Cc[2]) << 2) |
+                  ((uint32_t)keep_rule(mag_key(v.w), Pc[3], Mc[3], pos, Cc[3]) << 3);
         }
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
@@ -523,28 +532,44 @@ __device__ __forceinline__ void sparse_gram_rows(const float (*x)[xpitch(F)], co
         if (mask != nullptr && nib) atomicOr(mask + k, nib << (4 * q));
     }
     __syncwarp();
+    const int g = lane >> 3;
+    return min(g == 0 ? cnt[0] : g == 1 ? cnt[1] : g == 2 ? cnt[2] : cnt[3], lcap);
+}
+
+// Adds the listed positions of this lane's column to acc.
+template <int F>
+__device__ __forceinline__ void sparse_accum(const float (*x)[xpitch(F)], const float* r, int q, const uint16_t* list,
+                                             int lcap, int na, SparseAcc& acc) {
+    const int lane = threadIdx.x & 31;
     const int g = lane >> 3, j = lane & 7, a = 4 * q + g;
-    const int na = min(g == 0 ? cnt[0] : g == 1 ? cnt[1] : g == 2 ? cnt[2] : cnt[3], lcap);
     const uint16_t* la = list + g * lcap;
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, rh = 0.f;
     for (int t = 0; t < na; ++t) {
         const int k = la[t];
         const float xa = x[k][a];
         const float4 xb = reinterpret_cast<const float4*>(x[k])[j];
-        a0 = fmaf(xa, xb.x, a0);
-        a1 = fmaf(xa, xb.y, a1);
-        a2 = fmaf(xa, xb.z, a2);
-        a3 = fmaf(xa, xb.w, a3);
-        rh = fmaf(xa, r[k], rh);
+        acc.a0 = fmaf(xa, xb.x, acc.a0);
+        acc.a1 = fmaf(xa, xb.y, acc.a1);
+        acc.a2 = fmaf(xa, xb.z, acc.a2);
+        acc.a3 = fmaf(xa, xb.w, acc.a3);
+        acc.rh = fmaf(xa, r[k], acc.rh);
     }
+}
+
+// Stores the warp's four rows of [G | b] to dst (F x (F + 1)); with `diag`
+// the regulariser goes on the diagonal and padding rows (a >= f) become
+// identity rows, else the raw sums are stored (a split row's partial).
+template <int F>
+__device__ __forceinline__ void sparse_store(const SparseAcc& acc, int q, int f, float reg, bool diag, float* dst) {
+    const int lane = threadIdx.x & 31;
+    const int g = lane >> 3, j = lane & 7, a = 4 * q + g;
     float* row = dst + a * (F + 1);
-    const float v[4] = {a0, a1, a2, a3};
+    const float v[4] = {acc.a0, acc.a1, acc.a2, acc.a3};
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
         const int c = 4 * j + e;
-        row[c] = (a == c) ? ((a < f) ? v[e] + reg : 1.f) : v[e];
+        row[c] = (diag && a == c) ? ((a < f) ? v[e] + reg : 1.f) : v[e];
     }
-    if (j == 0) row[F] = rh;
+    if (j == 0) row[F] = acc.rh;
 }
 
 // ---------------------------------------------------------------------------
@@ -686,9 +711,13 @@ __global__ void __launch_bounds__(kCtaThreads, ENG == ENG_CUDA ? 4 : 1) k_cta_ro
     if constexpr (L::SPARSE) {
         if (sparse) {
             __syncwarp();
-            sparse_gram_rows<F>(s_x, s_r, n, f, reg, warp, s_P, s_Mk, s_cut, s_list + warp * 4 * L::list_cap(cap),
-                                L::list_cap(cap), masks_out != nullptr ? &s_mask[0][0] : nullptr,
-                                G_aug + (int64_t)w * F * (F + 1));
+            uint16_t* lw = s_list + warp * 4 * L::list_cap(cap);
+            const int na = sparse_list<F>(s_x, n, 0, nullptr, warp, s_P, s_Mk, s_cut, lw, L::list_cap(cap),
+                                          masks_out != nullptr ? &s_mask[0][0] : nullptr);
+            SparseAcc acc;
+            acc.zero();
+            sparse_accum<F>(s_x, s_r, warp, lw, L::list_cap(cap), na, acc);
+            sparse_store<F>(acc, warp, f, reg, true, G_aug + (int64_t)w * F * (F + 1));
             if (masks_out != nullptr) {
                 __syncthreads();
                 for (int e = tid; e < n * W; e += kCtaThreads) masks_out[lo * W + e] = (&s_mask[0][0])[e];

@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--no-large", action="store_true", help="skip the 10^8-cell n_f = 128 records")
     ap.add_argument("--no-sim", action="store_true", help="skip the simulation-design metrics")
     ap.add_argument("--no-probes", action="store_true", help="skip the roofline probes")
+    ap.add_argument("--no-warm", action="store_true", help="skip the learned warm-start record")
     return ap.parse_args()
 
 
@@ -605,53 +606,62 @@ def peaks_leg():
     return out
 
 
-def warmstart_arm(args):
+def warmstart_leg(budget=None, train_seeds=(101, 102, 103, 104, 105), held_seeds=(201, 202, 203, 204, 205),
+                  precisions=(0, 1, 2), epochs=20):
     """The learned warm start on the 100k x 20k shape: user and item nets
-    trained on the converged factors of 5 seeded matrices, judged on 5
-    held-out seeds against plain FP32 ALS from the same M^(0). For each
+    trained on the converged factors of the training seeds' matrices, judged
+    on held-out seeds against plain FP32 ALS from the same M^(0). For each
     held-out matrix: sweeps and CUDA-event ms to the plain run's final test
-    RMSE x (1 + 1e-3), for warm starts fitted in FP32, TF32 and BF16 (the
-    warm runs' times include computing the warm start)."""
+    RMSE x (1 + 1e-3), for warm starts fitted in each precision (the warm
+    runs' times include computing the warm start), the start the judging
+    rule keeps (the one ahead after 5 sweeps) and the gain."""
     import torch
     from paper_2509_18024_gb300 import warmstart
     w = dict(synth.WORKLOADS["zipf_100k"])
     f, lam = w["f"], w["lam"]
-    r = args.budget if args.budget is not None else w["budget"]
+    r = budget if budget is not None else w["budget"]
     sweeps = w["sweeps"]
 
     def draw(seed):
         return synth.zipf_ratings_device(w["n_u"], w["n_m"], w["f"], w["nnz"], w["zipf_s"], w["noise_sd"], seed)
 
     t0 = time.perf_counter()
-    nets, hist = warmstart.train([draw(s) for s in (101, 102, 103, 104, 105)], f, lam, r, sweeps=sweeps,
-                                 hidden=256, epochs=20, batch=4096)
+    nets, hist = warmstart.train([draw(s) for s in train_seeds], f, lam, r, sweeps=sweeps, hidden=256, epochs=epochs,
+                                 batch=4096)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     per_seed = []
-    for s in (201, 202, 203, 204, 205):
+    for s in held_seeds:
         prob = draw(s)
         M0 = synth.init_factor(w["n_m"], f, 5000 + s)
-        res = warmstart.judge(nets, prob, f, lam, r, M0, sweeps, precisions=(0, 1, 2))
+        res = warmstart.judge(nets, prob, f, lam, r, M0, sweeps, precisions=precisions)
         per_seed.append({"seed": s, "target_rmse": res["target"], "chosen": res["chosen"],
+                         "judge_after": res["judge_after"], "gain": res["gain"],
                          "warm_start_ms": res["warm_start_ms"],
                          "sweeps_to_target": {k: v for k, v in res["sweeps_to_target"].items() if k != "warm"},
                          "ms_to_target": res["ms_to_target"],
                          "rmse_per_sweep": {k: [round(e, 5) for e in v] for k, v in res["curves"].items()
                                             if k != "warm"}})
+
     def med(key, sub):
         vals = [d[key][sub] for d in per_seed if d[key][sub] is not None]
         return float(statistics.median(vals)) if vals else None
-    runs = ("plain", "warm_p0", "warm_p1", "warm_p2")
-    out = {"metric": "sweeps and ms to the plain FP32 run's final test RMSE (x 1.001)", "workload":
-           f"zipf_100k shape (device-drawn), n_f={f}, lambda={lam}, r={r}, {sweeps} sweeps; nets "
-           f"{f + 2}-256-256-{f} GELU, trained 20 epochs on 5 seeds", "train_s": round(train_s, 1),
-           "train_loss_first_last": {k: [v[0], v[-1]] for k, v in hist.items()},
-           "median_sweeps": {k: med("sweeps_to_target", k) for k in runs},
-           "median_ms": {k: med("ms_to_target", k) for k in runs},
-           "runs": {"plain": "FP32 from random M^(0)", "warm_p0": "warm start, FP32",
-                    "warm_p1": "warm start, TF32 + 1 refinement", "warm_p2": "warm start, BF16 + 2 refinements"},
-           "per_seed": per_seed}
-    print(json.dumps(out), flush=True)
+    runs = ("plain",) + tuple(f"warm_p{q}" for q in precisions)
+    names = {"plain": "FP32 from random M^(0)", "warm_p0": "warm start, FP32",
+             "warm_p1": "warm start, TF32 + 1 refinement", "warm_p2": "warm start, BF16 + 2 refinements"}
+    return {"metric": "sweeps and ms to the plain FP32 run's final test RMSE (x 1.001)", "workload":
+            f"zipf_100k shape (device-drawn), n_f={f}, lambda={lam}, r={r}, {sweeps} sweeps; nets "
+            f"{f + 2}-256-256-{f} GELU, trained {epochs} epochs on {len(train_seeds)} seeds",
+            "train_s": round(train_s, 1),
+            "train_loss_first_last": {k: [v[0], v[-1]] for k, v in hist.items()},
+            "median_sweeps": {k: med("sweeps_to_target", k) for k in runs},
+            "median_ms": {k: med("ms_to_target", k) for k in runs},
+            "warm_start_chosen": sum(d["chosen"] == "warm" for d in per_seed), "held_out_seeds": len(per_seed),
+            "runs": {k: names[k] for k in runs}, "per_seed": per_seed}
+
+
+def warmstart_arm(args):
+    print(json.dumps(warmstart_leg(args.budget)), flush=True)
 
 
 def batch_arm(args):
@@ -820,6 +830,9 @@ def main():
                                              f"(est. {t_sweep:.1f} s per sweep)"}
         if world == 1 and not args.no_sim:
             out["simulation_metrics"] = simulation_leg()
+        if world == 1 and not args.no_warm:
+            out["warm_start"] = warmstart_leg(train_seeds=(101, 102, 103), held_seeds=(201, 202),
+                                              precisions=(0, 2), epochs=12)
         if world == 1 and not args.no_large:
             import torch
             eng.close()

@@ -165,6 +165,15 @@ int als_get_options(const als_handle* h, als_options* opt_host);
  * monotone indptr, finite values) and build its row plan (rows bucketed by
  * length). Synchronises the stream. Later calls with the same indptr
  * pointer, n_rows and nnz reuse the plan; other calls prepare implicitly.
+ * Every call that reuses a plan checks the buffers again on the device,
+ * without synchronising (also inside a captured graph, on every replay):
+ * if their indices or values were refilled with invalid ones, the next call
+ * that reads the device error words (als_get_report, als_fit, als_fit_host)
+ * returns ALS_ERR_CSR or ALS_ERR_NONFINITE, and the results since the last
+ * report are not valid. Kernels clamp out-of-range indices, so such buffers
+ * never make a gather read outside the factor. A refilled indptr (changed
+ * row structure) must be announced by calling als_prepare again, which
+ * re-validates synchronously and rebuilds the plan when the rows changed.
  * Call it once per structure before capturing work into a CUDA graph. */
 int als_prepare(als_handle* h, const als_csr* R_side);
 

@@ -325,6 +325,9 @@ constexpr size_t kMiscBytes = kDevErrOffset + 16;
 // Sticky device error word: bit 0 = a bounded device wait ran out. Kernels
 // set it; the host reads and clears it when it synchronises for a report.
 unsigned* dev_err(als_handle* h) { return reinterpret_cast<unsigned*>(static_cast<char*>(h->misc.p) + kDevErrOffset); }
+// Structure check of a reused plan's buffers (k_validate bits, written
+// without synchronising); read and cleared with the error word.
+unsigned* reuse_err(als_handle* h) { return dev_err(h) + 1; }
 
 // Status of a device error word value read back by the host (which then clears the word).
 int dev_err_status(als_handle* h, unsigned e) {
@@ -356,9 +359,12 @@ int validate_csr(als_handle* h, const als_csr* R, std::vector<int64_t>& indptr) 
     return ALS_OK;
 }
 
-int build_plan(als_handle* h, const als_csr* R, Plan** out) {
+// *reused: the plan was found in the cache without a synchronous check; the
+// caller then re-checks the indices and values on the device (asynchronously).
+int build_plan(als_handle* h, const als_csr* R, Plan** out, bool* reused = nullptr) {
     std::vector<int64_t> indptr;
     bool checked = false;
+    if (reused) *reused = false;
     for (size_t q = 0; q < h->plans.size(); ++q) {
         Plan& p = h->plans[q];
         if (p.indptr == R->indptr && p.n_rows == R->n_rows && p.nnz == R->nnz && p.n_cols == R->n_cols &&
@@ -366,6 +372,7 @@ int build_plan(als_handle* h, const als_csr* R, Plan** out) {
             p.tuning.tc_gram == h->tuning.tc_gram) {
             if (!p.stale) {
                 *out = &p;
+                if (reused) *reused = true;
                 return ALS_OK;
             }
             // The buffers were refilled: validate the new contents; the plan
@@ -811,9 +818,11 @@ int launch_fp64(als_handle* h, const Side& side, const Params& p, const uint32_t
 }
 
 // mode 0: solve into X_out; 1: assembled systems into G_out/b_out; 2: masks only.
+// revalidate: the plan was reused from the cache, so the buffers' indices and
+// values are checked again on the device, beside the row work.
 template <int F, int ENG>
 int run_side(als_handle* h, const Plan& pl, const Side& side, int mode, float* X_out, int32_t* flags_out,
-             uint32_t* masks_out, float* G_out, float* b_out) {
+             uint32_t* masks_out, float* G_out, float* b_out, bool revalidate) {
     cudaStream_t st = h->stream;
     Params p = make_params(h->opt);
     p.err = dev_err(h);
@@ -884,6 +893,18 @@ int run_side(als_handle* h, const Plan& pl, const Side& side, int mode, float* X
         if (rc) return rc;
         ALS_CUDA(h, cudaEventRecord(h->ev_fork, st));
     }
+    if (revalidate && pl.n_rows > 0) {
+        // On the warp-row stream when the groups overlap (it finishes first).
+        if (overlap) {
+            ALS_CUDA(h, cudaStreamWaitEvent(h->aux2, h->ev_fork, 0));
+            h->stream = h->aux2;
+        }
+        const int blocks = (int)std::min<int64_t>((std::max(pl.n_rows, pl.nnz) + 255) / 256, (int64_t)h->n_sm * 8);
+        ALS_LAUNCH(h, "validate", als::k_validate<<<blocks, 256, 0, h->stream>>>(side.indptr, side.indices,
+                                                                              side.values, pl.n_rows, pl.n_cols,
+                                                                              pl.nnz, reuse_err(h)));
+        h->stream = st;
+    }
     if (pl.n_slots > 0) {
         if (overlap) {
             ALS_CUDA(h, cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
@@ -940,7 +961,12 @@ int run_side(als_handle* h, const Plan& pl, const Side& side, int mode, float* X
     }
     if (overlap) {
         if (pl.n_slots > 0) ALS_CUDA(h, cudaStreamWaitEvent(st, h->ev_join, 0));
-        if (F <= 32 && n_warp > 0) ALS_CUDA(h, cudaStreamWaitEvent(st, h->ev_join2, 0));
+        if (F <= 32 && n_warp > 0) {
+            ALS_CUDA(h, cudaStreamWaitEvent(st, h->ev_join2, 0));
+        } else if (revalidate && pl.n_rows > 0) {
+            ALS_CUDA(h, cudaEventRecord(h->ev_join2, h->aux2));
+            ALS_CUDA(h, cudaStreamWaitEvent(st, h->ev_join2, 0));
+        }
     }
     if (mode == 1 && n_aug > 0)
         ALS_LAUNCH(h, "unpack_aug", als::k_unpack_aug<F><<<1024, 256, 0, st>>>(G_aug, lists, n_aug, p.f, G_out, b_out));
@@ -992,7 +1018,7 @@ int run_side(als_handle* h, const Plan& pl, const Side& side, int mode, float* X
 
 // All built (width, engine) pairs.
 int run_side_any(als_handle* h, const Plan& pl, const Side& side, int mode, float* X_out, int32_t* flags_out,
-                 uint32_t* masks_out, float* G_out, float* b_out) {
+                 uint32_t* masks_out, float* G_out, float* b_out, bool revalidate) {
     int F = padded_width(h->opt.n_f, h->opt.precision);
     int eng = engine_of(h->opt.precision, F);
     if (h->tuning.tc_gram && h->opt.precision == ALS_FP32 && F <= 32) {
@@ -1000,7 +1026,8 @@ int run_side_any(als_handle* h, const Plan& pl, const Side& side, int mode, floa
         eng = als::ENG_TF32X3;
     }
 #define ALS_RUN(FF, EE)                                                                          \
-    if (F == FF && eng == EE) return run_side<FF, EE>(h, pl, side, mode, X_out, flags_out, masks_out, G_out, b_out)
+    if (F == FF && eng == EE)                                                                     \
+        return run_side<FF, EE>(h, pl, side, mode, X_out, flags_out, masks_out, G_out, b_out, revalidate)
     ALS_RUN(8, als::ENG_CUDA);
     ALS_RUN(16, als::ENG_CUDA);
     ALS_RUN(32, als::ENG_CUDA);
@@ -1023,7 +1050,8 @@ int dispatch_side(als_handle* h, const als_csr* R, const float* Y, int mode, flo
     if (rc) return rc;
     if (!Y && R->n_cols > 0) return set_err(h, ALS_ERR_ARG, "factor Y is null");
     Plan* pl = nullptr;
-    rc = build_plan(h, R, &pl);
+    bool reused = false;
+    rc = build_plan(h, R, &pl, &reused);
     if (rc) return rc;
     Side side;
     side.indptr = R->indptr;
@@ -1033,7 +1061,7 @@ int dispatch_side(als_handle* h, const als_csr* R, const float* Y, int mode, flo
     side.n_rows = R->n_rows;
     side.n_cols = R->n_cols;
     if (mode == 0) ALS_CUDA(h, cudaMemsetAsync(counters(h), 0, sizeof(Counters), h->stream));
-    return run_side_any(h, *pl, side, mode, X_out, flags_out, masks_out, G_out, b_out);
+    return run_side_any(h, *pl, side, mode, X_out, flags_out, masks_out, G_out, b_out, reused);
 }
 
 template <int F>
@@ -1139,6 +1167,10 @@ int als_prepare(als_handle* h, const als_csr* R) {
     if (!h) return ALS_ERR_ARG;
     int rc = check_csr(h, R);
     if (rc) return rc;
+    // A cached plan on these buffers is checked again, synchronously: its
+    // structure is re-validated and the plan rebuilt if the rows changed.
+    for (Plan& p : h->plans)
+        if (p.indptr == R->indptr) p.stale = true;
     Plan* pl = nullptr;
     return build_plan(h, R, &pl);
 }
@@ -1326,10 +1358,11 @@ int als_kernel_time(als_handle* h, const char* name, double* ms_host, int64_t* l
 int als_get_report(als_handle* h, als_report* rep) {
     if (!h || !rep) return ALS_ERR_ARG;
     Counters c;
-    unsigned e = 0;
+    unsigned words[2] = {0u, 0u};  // error word, reused-structure check
     ALS_CUDA(h, cudaMemcpyAsync(&c, counters(h), sizeof c, cudaMemcpyDeviceToHost, h->stream));
-    ALS_CUDA(h, cudaMemcpyAsync(&e, dev_err(h), sizeof e, cudaMemcpyDeviceToHost, h->stream));
+    ALS_CUDA(h, cudaMemcpyAsync(words, dev_err(h), sizeof words, cudaMemcpyDeviceToHost, h->stream));
     ALS_CUDA(h, cudaStreamSynchronize(h->stream));
+    const unsigned e = words[0];
     std::memset(rep, 0, sizeof *rep);
     rep->rows_flagged = (int64_t)c.flagged;
     rep->rows_singular = (int64_t)c.singular;
@@ -1339,6 +1372,14 @@ int als_get_report(als_handle* h, als_report* rep) {
     rep->max_pivot_ratio = mr;
     rep->test_rmse = NAN;
     rep->objective = NAN;
+    if (words[1] != 0u) {
+        ALS_CUDA(h, cudaMemsetAsync(reuse_err(h), 0, sizeof(unsigned), h->stream));
+        if (e) dev_err_status(h, e);  // clear it too
+        if (words[1] & 3u)
+            return set_err(h, ALS_ERR_CSR, "refilled buffers of a cached plan hold out-of-range, unsorted or duplicate "
+                                           "indices or a bad indptr: results since the last report are not valid");
+        return set_err(h, ALS_ERR_NONFINITE, "refilled buffers of a cached plan hold a non-finite rating");
+    }
     return dev_err_status(h, e);
 }
 

@@ -69,6 +69,14 @@ struct Fallback {
     unsigned int* count;
 };
 
+// A column index of the rating structure as a row of the other side's factor
+// (n_cols rows): indices outside [0, n_cols) - possible only when validated
+// buffers were refilled in place, which the next report then flags - are
+// clamped, so that no gather reads outside the factor.
+__device__ __forceinline__ int32_t factor_row(int32_t j, int64_t n_cols) {
+    return (uint32_t)j < (uint64_t)n_cols ? j : (j < 0 ? 0 : (int32_t)(n_cols - 1));
+}
+
 // |x| as an order-preserving unsigned key: for finite floats the unsigned
 // order of the sign-cleared bit pattern is the order of |x|; -0 and +0 tie.
 __device__ __forceinline__ uint32_t mag_key(float x) { return __float_as_uint(x) & 0x7fffffffu; }

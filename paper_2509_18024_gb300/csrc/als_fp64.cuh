@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(kFp64Threads) k_fp64_rows(Side side, Params p,
         for (int c0 = 0; c0 < n; c0 += kFp64Chunk) {
             const int cn = min(kFp64Chunk, n - c0);
             for (int k = tid; k < cn; k += kFp64Threads) {
-                S.idx[k] = side.indices[lo + c0 + k];
+                S.idx[k] = factor_row(side.indices[lo + c0 + k], side.n_cols);
                 S.r[k] = side.values[lo + c0 + k];
             }
             for (int e = tid; e < cn * W; e += kFp64Threads) (&S.mask[0][0])[e] = masks[(lo + c0) * W + e];
@@ -140,7 +140,7 @@ __device__ __forceinline__ void resid_range(const Side& side, const Params& p, c
         uint32_t keep = 0u;
         float rk = 0.f;
         if (valid) {
-            const int32_t j = side.indices[lo + k];
+            const int32_t j = factor_row(side.indices[lo + k], side.n_cols);
             rk = side.values[lo + k];
             keep = masks[(lo + k) * R::W + (c0 >> 5)] >> (c0 & 31);
             if (vec) {

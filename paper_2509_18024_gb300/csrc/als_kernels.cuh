@@ -47,10 +47,10 @@ __global__ void __launch_bounds__(256, 4) k_warp_rows(Side side, Params p, const
     const int f = p.f;
     const int64_t i = rows[w];
     const int64_t lo = side.indptr[i];
-    const int n = (int)(side.indptr[i + 1] - lo);
+    const int n = min((int)(side.indptr[i + 1] - lo), kWarpRowMax);  // the plan's bound
 
     if (lane < n) {
-        T.idx[lane] = side.indices[lo + lane];
+        T.idx[lane] = factor_row(side.indices[lo + lane], side.n_cols);
         T.r[lane] = side.values[lo + lane];
     }
     __syncwarp();

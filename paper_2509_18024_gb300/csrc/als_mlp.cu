@@ -168,8 +168,11 @@ __global__ void k_to_bf16(const float* __restrict__ w, __nv_bfloat16* __restrict
 
 // Features, one warp per row.
 __global__ void k_features(const int64_t* __restrict__ indptr, const int32_t* __restrict__ indices,
-                           const float* __restrict__ values, int64_t n_rows, const float* __restrict__ Y, int f,
-                           float* __restrict__ out) {
+                           const float* __restrict__ values, int64_t n_rows, int64_t n_cols,
+                           const float* __restrict__ Y, int f, float* __restrict__ out) {
+    // One warp per row; lanes take the row's entries lane, lane + 32, ...
+    // and keep partial sums of up to 32 feature columns at a time, which meet
+    // by a fixed butterfly (the same order every run).
     const int lane = threadIdx.x & 31;
     const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (i >= n_rows) return;
@@ -180,10 +183,29 @@ __global__ void k_features(const int64_t* __restrict__ indptr, const int32_t* __
 #pragma unroll
     for (int o = 16; o; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
     float* dst = out + i * (f + 2);
-    for (int a = lane; a < f; a += 32) {
-        float acc = 0.f;
-        for (int64_t e = lo; e < hi; ++e) acc = fmaf(values[e], Y[(int64_t)indices[e] * f + a], acc);
-        dst[a] = (n > 0 && rs != 0.f) ? acc / rs : 0.f;
+    for (int a0 = 0; a0 < f; a0 += 32) {
+        const int na = min(32, f - a0);
+        float acc[32];
+#pragma unroll
+        for (int q = 0; q < 32; ++q) acc[q] = 0.f;
+        for (int64_t e = lo + lane; e < hi; e += 32) {
+            const int32_t j = indices[e];
+            if ((uint32_t)j >= (uint64_t)n_cols) continue;
+            const float v = values[e];
+            const float* y = Y + (int64_t)j * f + a0;
+#pragma unroll
+            for (int q = 0; q < 32; ++q)
+                if (q < na) acc[q] = fmaf(v, y[q], acc[q]);
+        }
+        float mine = 0.f;
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+            float t = acc[q];
+#pragma unroll
+            for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == q) mine = t;
+        }
+        if (lane < na) dst[a0 + lane] = (n > 0 && rs != 0.f) ? mine / rs : 0.f;
     }
     if (lane == 0) {
         dst[f] = logf(1.f + (float)n);
@@ -443,7 +465,7 @@ int als_features(const als_csr* R, const float* Y, int n_f, float* feat, void* s
     if (R->n_rows == 0) return ALS_OK;
     const int64_t threads = R->n_rows * 32;
     k_features<<<(int)((threads + 255) / 256), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
-        R->indptr, R->indices, R->values, R->n_rows, Y, n_f, feat);
+        R->indptr, R->indices, R->values, R->n_rows, R->n_cols, Y, n_f, feat);
     return cudaGetLastError() == cudaSuccess ? ALS_OK : ALS_ERR_CUDA;
 }
 

@@ -134,7 +134,7 @@ template <int F>
 __device__ __forceinline__ void stage_tile(float (*x)[xpitch(F)], float* r, int32_t* idx, const Side& side, int f,
                                            int64_t e0, int cn) {
     for (int k = threadIdx.x; k < cn; k += kCtaThreads) {
-        idx[k] = side.indices[e0 + k];
+        idx[k] = factor_row(side.indices[e0 + k], side.n_cols);
         r[k] = side.values[e0 + k];
     }
     __syncthreads();
@@ -683,7 +683,7 @@ __global__ void __launch_bounds__(kCtaThreads, ENG == ENG_CUDA ? 4 : 1) k_cta_ro
     __syncthreads();
     const int64_t i = rows[w];
     const int64_t lo = side.indptr[i];
-    const int n = (int)(side.indptr[i + 1] - lo);
+    const int n = min((int)(side.indptr[i + 1] - lo), cap);  // the plan's bound on this launch's rows
     // The budget and regulariser take FP64 steps (a slow pipe here): one
     // thread evaluates them; stage_tile's barrier publishes them.
     if (tid == 0) {
@@ -867,7 +867,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_split_hist(Side side, Params p,
 #pragma unroll
             for (int u = 0; u < B; ++u) {
                 const int k = kb + u * kstep;
-                j[u] = k < len ? side.indices[e0 + k] : -1;
+                j[u] = k < len ? factor_row(side.indices[e0 + k], side.n_cols) : -1;
             }
             float4 v[B];
 #pragma unroll
@@ -943,7 +943,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_split_eqcount(Side side, Params
         const int64_t e0 = ci.lo + ci.start;
         int local = 0;
         for (int k = k0; k < ci.len; k += kstep) {
-            const int32_t j = side.indices[e0 + k];
+            const int32_t j = factor_row(side.indices[e0 + k], side.n_cols);
             local += mag_key(__ldg(side.Y + (int64_t)j * p.f + a_t)) == T;
         }
         if (local) atomicAdd(&cnt[a_t], local);
@@ -979,7 +979,8 @@ __global__ void k_split_cut(Side side, Params p, SplitPlan sp, SplitState st) {
         for (int kb = 0; kb < ci.len; kb += 32) {
             const int k = kb + lane;
             bool eq = false;
-            if (k < ci.len) eq = mag_key(__ldg(side.Y + (int64_t)side.indices[e0 + k] * p.f + a)) == T;
+            if (k < ci.len)
+                eq = mag_key(__ldg(side.Y + (int64_t)factor_row(side.indices[e0 + k], side.n_cols) * p.f + a)) == T;
             unsigned b = __ballot_sync(kFull, eq);
             const int c = __popc(b);
             if (seen + c >= nd) {

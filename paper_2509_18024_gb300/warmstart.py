@@ -6,8 +6,11 @@ They are trained on factors that ALS itself converged to on seeded training
 matrices (inputs from the converged other side, targets the converged rows).
 At use time, from a random M^(0): U_w = user_net(features(R, M^(0))),
 M_w = item_net(features(R^T, U_w)), and ALS starts from M_w. Plain ALS from
-M^(0) is the judge: if the warm start's test RMSE after the first sweep is
-worse, the fit falls back to M^(0).
+M^(0) is the judge: both starts run `judge_after` sweeps (default 5), and the
+fit continues from the warm start only if its test RMSE there is not worse;
+otherwise it falls back to M^(0). The gain is reported as sweeps and
+milliseconds to the target RMSE saved by the warm start (negative when it
+loses).
 
 This module only orchestrates; features, the networks (forward, backward,
 Adam) and ALS run in libcore_als.so.
@@ -84,12 +87,14 @@ def warm_factor(nets: Pair, Ru, Ri, M0: torch.Tensor, n_f: int):
     return nets.items.forward(core_als.features(Ri, Uw, n_f))
 
 
-def judge(nets: Pair, problem, n_f, lam, budget, M0, sweeps, target=None, precisions=(0,)):
+def judge(nets: Pair, problem, n_f, lam, budget, M0, sweeps, target=None, precisions=(0,), judge_after=5):
     """Test RMSE per sweep from M^(0) (plain ALS, FP32) and from the warm start
     (one run per precision in `precisions`), the chosen start (warm unless its
-    first-sweep RMSE is worse) and the sweeps and CUDA-event milliseconds each
-    run needs to reach `target` (default: the plain run's final RMSE x
-    (1 + 1e-3)). A warm run's time includes computing the warm start."""
+    RMSE after `judge_after` sweeps is worse than the plain run's), the sweeps
+    and CUDA-event milliseconds each run needs to reach `target` (default: the
+    plain run's final RMSE x (1 + 1e-3)), and the gain of the first warm run
+    over the plain one in both (None where a run never reaches the target). A
+    warm run's time includes computing the warm start."""
     Ru, Ri, test = device_sides(problem)
     M0d = torch.as_tensor(M0).cuda()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -123,11 +128,16 @@ def judge(nets: Pair, problem, n_f, lam, budget, M0, sweeps, target=None, precis
     if target is None:
         target = curves["plain"][-1] * (1 + 1e-3)
     first_warm = f"warm_p{precisions[0]}"
-    chosen = "warm" if curves[first_warm][0] <= curves["plain"][0] else "plain"
-    reach = {k: next((q + 1 for q, e in enumerate(v) if e <= target), None) for k, v in curves.items()}
-    reach_ms = {k: (times[k][reach[k] - 1] if reach[k] else None) for k in curves}
-    out = {"target": target, "curves": curves, "chosen": chosen, "sweeps_to_target": reach,
-           "ms_to_target": reach_ms, "warm_start_ms": warm_ms}
+    k = max(1, min(judge_after, sweeps))
+    chosen = "warm" if curves[first_warm][k - 1] <= curves["plain"][k - 1] else "plain"
+    reach = {key: next((q + 1 for q, e in enumerate(v) if e <= target), None) for key, v in curves.items()}
+    reach_ms = {key: (times[key][reach[key] - 1] if reach[key] else None) for key in curves}
+    gain = {"sweeps_saved": (reach["plain"] - reach[first_warm]) if reach["plain"] and reach[first_warm] else None,
+            "ms_saved": (reach_ms["plain"] - reach_ms[first_warm]) if reach["plain"] and reach[first_warm] else None,
+            "rmse_at_judge": {"plain": curves["plain"][k - 1], "warm": curves[first_warm][k - 1]},
+            "final_rmse": {"plain": curves["plain"][-1], "warm": curves[first_warm][-1]}}
+    out = {"target": target, "curves": curves, "chosen": chosen, "judge_after": k, "sweeps_to_target": reach,
+           "ms_to_target": reach_ms, "warm_start_ms": warm_ms, "gain": gain}
     out["curves"]["warm"] = curves[first_warm]
     out["sweeps_to_target"]["warm"] = reach[first_warm]
     return out

@@ -366,3 +366,32 @@ def test_full_size_sampled_rows(core, zipf, side):
     take = np.concatenate([np.arange(csr.indptr[i], csr.indptr[i + 1]) for i in sample])
     mo = oracle.select_half(sub_ptr, csr.indices[take], Y.astype(np.float64), r)
     assert np.array_equal(masks[take], mo)
+
+
+def test_refilled_buffers_with_invalid_entries_are_reported(core):
+    # A cached plan trusts its buffers' identity; refilling them in place with
+    # an out-of-range index or a NaN rating is caught by the device-side check
+    # that every reuse runs, and the next report returns the error. The
+    # clamped gathers keep the results finite meanwhile.
+    from paper_2509_18024_gb300 import binding as B
+    csr, Y = rows_problem(LENGTHS, 4000, 32, seed=9)
+    eng = core.CoreALS(32, 0.05, 0.25)
+    R = core.DeviceCSR.from_host(csr)
+    Yd = torch.as_tensor(Y).cuda()
+    X = eng.half_sweep(R, Yd)
+    eng.report()
+    for field, at, bad, status in (("indices", 40, 4007, -2), ("values", 41, float("nan"), -3),
+                                   ("indices", 5500, -3, -2)):
+        buf = getattr(R, field)
+        keep = buf[at].item()
+        buf[at] = bad
+        X = eng.half_sweep(R, Yd)
+        assert torch.isfinite(X).all() or field == "values"
+        with pytest.raises(B.AlsError) as e:
+            eng.report()
+        assert e.value.status == status, (field, e.value.status)
+        buf[at] = keep
+        X = eng.half_sweep(R, Yd)
+        eng.report()  # clean again
+    Xo, _, _ = oracle_half(csr, Y, 0.05, 0.25)
+    assert rel_fro(X.cpu().numpy(), Xo) <= HALF_TOL

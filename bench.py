@@ -283,21 +283,19 @@ KERNEL_FAMILIES = ("cta_rows", "warp_rows", "solve_rows", "split_init", "split_h
 # summarised in profiles/cta_rows_zipf100k_traffic.md (dram__bytes_read.sum +
 # dram__bytes_write.sum, summed over the k_cta_rows launches of one sweep;
 # `roofline.traffic` is that sum over the sweep's measured launches). It
-# holds only for the kernel sources it was taken from: `roofline.traffic` is
-# null once their hash differs.
-TRAFFIC = {"kernel": "cta_rows", "bytes_per_sweep": 295.3e6, "sources_sha256_16": "b7282143df965677"}
+# holds only for the kernel's sources it was taken from: `roofline.traffic`
+# is null once they hash differently.
+TRAFFIC = {"kernel": "cta_rows", "bytes_per_sweep": 295.2e6, "sources_sha256_16": "1bca918151f341d7",
+           "sources": ("als_device.cuh", "als_rows.cuh", "als_tc.cuh")}
 
 
-def kernel_sources_hash():
-    import glob
+def kernel_sources_hash(files=TRAFFIC["sources"]):
     import hashlib
     pkg = os.path.join(ROOT, "paper_2509_18024_gb300", "csrc")
-    files = sorted(glob.glob(os.path.join(pkg, "*.cu")) + glob.glob(os.path.join(pkg, "*.cuh")))
-    files.append(os.path.join(ROOT, "include", "core_als.h"))
     h = hashlib.sha256()
     for fn in files:
-        h.update(os.path.basename(fn).encode())
-        with open(fn, "rb") as fh:
+        h.update(fn.encode())
+        with open(os.path.join(pkg, fn), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 

@@ -1255,8 +1255,8 @@ int als_objective(als_handle* h, const als_csr* Ru, const als_csr* Ri, const flo
     double* part = static_cast<double*>(h->evalbuf.p);
     double* out = part + 3 * als_eval::kBlocks;
     cudaStream_t st = h->stream;
-    cudaError_t e = als_eval::objective(st, Ru->indptr, Ru->indices, Ru->values, Ru->n_rows, Ri->indptr, Ri->n_rows,
-                                        U, M, h->opt.n_f, (double)h->opt.lambda,
+    cudaError_t e = als_eval::objective(st, Ru->indptr, Ru->indices, Ru->values, Ru->n_rows, Ru->nnz, Ri->indptr,
+                                        Ri->n_rows, U, M, h->opt.n_f, (double)h->opt.lambda,
                                         h->opt.reg_mode == ALS_REG_PLAIN ? 1 : 0, part, out);
     h->launches += 4;
     if (e != cudaSuccess) return set_err(h, ALS_ERR_CUDA, "objective launch failed: %s", cudaGetErrorString(e));

@@ -54,22 +54,35 @@ __device__ __forceinline__ double block_sum256(double v, double* red) {
 }
 
 // Data term of the objective: sum over the training entries of one side's
-// rows of (r_e - u_i . m_{j_e})^2. A warp per row (grid-stride over rows),
-// lanes over the row's entries.
+// rows of (r_e - u_i . m_{j_e})^2. Entry-parallel, so that long rows do not
+// serialise: warp w takes the contiguous entries [w C, (w + 1) C) (C a
+// multiple of 32), lane l its entries w C + l + 32 t; each lane finds the row
+// of its first entry by binary search of indptr and then walks forward.
 __global__ void __launch_bounds__(256) k_obj_data(const int64_t* __restrict__ indptr,
                                                   const int32_t* __restrict__ indices,
                                                   const float* __restrict__ values, int64_t n_rows, int64_t n_cols,
-                                                  const float* __restrict__ U, const float* __restrict__ M, int f,
-                                                  double* __restrict__ partials) {
+                                                  int64_t nnz, const float* __restrict__ U,
+                                                  const float* __restrict__ M, int f, double* __restrict__ partials) {
     __shared__ double red[256];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * 8;
+    const int64_t w = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int64_t chunk = ((nnz + warps - 1) / warps + 31) / 32 * 32;
+    const int64_t e0 = w * chunk + lane, e1 = min(nnz, (w + 1) * chunk);
     double acc = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * 8 + warp; i < n_rows; i += (int64_t)gridDim.x * 8) {
-        const float* u = U + i * f;
-        for (int64_t e = indptr[i] + lane; e < indptr[i + 1]; e += 32) {
+    if (e0 < e1 && n_rows > 0) {
+        int64_t lo = 0, hi = n_rows;  // the row i with indptr[i] <= e0 < indptr[i + 1]
+        for (int it = 0; it < 64 && hi - lo > 1; ++it) {
+            const int64_t mid = lo + (hi - lo) / 2;
+            if (indptr[mid] <= e0) lo = mid;
+            else hi = mid;
+        }
+        int64_t i = lo;
+        for (int64_t e = e0; e < e1; e += 32) {
+            while (i + 1 < n_rows && indptr[i + 1] <= e) ++i;
             const int32_t j = indices[e];
             if ((uint32_t)j >= (uint64_t)n_cols) continue;  // never read outside M
-            const double d = (double)values[e] - (double)predict_vec(u, M + (int64_t)j * f, f);
+            const double d = (double)values[e] - (double)predict_vec(U + i * f, M + (int64_t)j * f, f);
             acc += d * d;
         }
     }
@@ -285,9 +298,9 @@ __global__ void __launch_bounds__(kRankThreads) k_rank(int64_t n_u, int64_t n_m,
 }  // namespace
 
 cudaError_t objective(cudaStream_t st, const int64_t* u_indptr, const int32_t* u_indices, const float* u_values,
-                      int64_t n_u, const int64_t* m_indptr, int64_t n_m, const float* U, const float* M, int f,
-                      double lambda, int plain_reg, double* partials, double* out_dev) {
-    k_obj_data<<<kBlocks, 256, 0, st>>>(u_indptr, u_indices, u_values, n_u, n_m, U, M, f, partials);
+                      int64_t n_u, int64_t u_nnz, const int64_t* m_indptr, int64_t n_m, const float* U,
+                      const float* M, int f, double lambda, int plain_reg, double* partials, double* out_dev) {
+    k_obj_data<<<kBlocks, 256, 0, st>>>(u_indptr, u_indices, u_values, n_u, n_m, u_nnz, U, M, f, partials);
     k_obj_reg<<<kBlocks, 256, 0, st>>>(u_indptr, n_u, U, f, plain_reg, partials + kBlocks);
     k_obj_reg<<<kBlocks, 256, 0, st>>>(m_indptr, n_m, M, f, plain_reg, partials + 2 * kBlocks);
     k_sum_groups<<<1, 32, 0, st>>>(partials, kBlocks, 3, 1, lambda, out_dev);

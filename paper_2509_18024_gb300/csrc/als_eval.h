@@ -17,8 +17,8 @@ constexpr int kRankThreads = 256;
 // Partials needed by objective(): 3 * kBlocks doubles, plus 1 for the result.
 // out_dev = data term + lambda * (penalty of U + penalty of M).
 cudaError_t objective(cudaStream_t st, const int64_t* u_indptr, const int32_t* u_indices, const float* u_values,
-                      int64_t n_u, const int64_t* m_indptr, int64_t n_m, const float* U, const float* M, int f,
-                      double lambda, int plain_reg, double* partials, double* out_dev);
+                      int64_t n_u, int64_t u_nnz, const int64_t* m_indptr, int64_t n_m, const float* U,
+                      const float* M, int f, double lambda, int plain_reg, double* partials, double* out_dev);
 
 // Partials: 2 * kBlocks doubles. out_dev[0] = sum_E (r - u.m)^2, out_dev[1] = sum_E r^2.
 cudaError_t sse_and_norm(cudaStream_t st, int64_t n, const int32_t* iu, const int32_t* im, const float* r,

@@ -417,7 +417,12 @@ int als_batch_destroy(als_batch* b);
  * and a 3-layer MLP  y = W3 GELU(W2 GELU(W1 x + b1) + b2) + b3  (GELU with
  * erf) trained on MSE by Adam (beta 0.9 / 0.999, eps 1e-8). Master weights
  * are FP32; the forward and backward products use their BF16 rounding;
- * activations and sums are FP32 and every reduction has a fixed order.
+ * activations and sums are FP32 and every reduction has a fixed order. The
+ * products run on the tensor cores (tcgen05 kind::tf32; BF16 weights are
+ * exact in TF32, FP32 operands are split into TF32 hi + lo parts). A bounded
+ * tensor-core wait that runs out is returned as ALS_ERR_TIMEOUT by the next
+ * call of the network that synchronises (grad, train_step with a loss,
+ * get_params).
  * Parameters (FP32, flat): W1 (hidden x in), b1, W2 (hidden x hidden), b2,
  * W3 (out x hidden), b3. X, Y, T are device arrays, row-major. */
 typedef struct als_mlp als_mlp;

@@ -10,6 +10,12 @@
 // for the forward and backward products; activations and all sums are FP32.
 // Reductions over rows (weight gradients, loss) are split into fixed blocks
 // and summed in a fixed order, so results are deterministic.
+//
+// Every product runs on the tensor cores (tcgen05.mma kind::tf32, FP32
+// accumulator in tensor memory): a BF16 weight is exact in TF32, and an FP32
+// operand x is split as x = hi + lo with hi its TF32 rounding, so that
+// W x = W hi + W lo, and A B = hi hi + hi lo + lo hi for two FP32 operands,
+// which keeps the products at FP32 accuracy.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -18,13 +24,13 @@
 #include <cstring>
 #include <vector>
 
+#include <type_traits>
+
 #include "core_als.h"
+#include "als_tc.cuh"
 
 namespace {
 
-constexpr int kTile = 64;     // output tile
-constexpr int kTileK = 16;    // reduction slice
-constexpr int kThreads = 256; // 16 x 16 threads, 4 x 4 outputs each
 constexpr int kSplitRows = 4096;  // rows per partial of a weight gradient
 
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
@@ -37,53 +43,161 @@ __device__ __forceinline__ float gelu_grad(float z) {
 // C[m][n] = sum_k A(m, k) B(k, n) (+ bias[n]), A(m, k) = TA ? A[k][m] : A[m][k]
 // (leading dimension lda), B(k, n) = TB ? B[n][k] : B[k][n] (ldb). B may be
 // BF16 (weights). k runs over [k0, k1). Output row-major with ldc.
+//
+// One CTA of 128 threads per tile of 128 rows x up to 256 columns: per
+// chunk of 32 k the threads convert their rows of A and B into the
+// canonical K-major, no-swizzle core-matrix layout of als_tc.cuh (TF32 hi
+// and lo parts), thread 0 issues the MMAs into the tile's TMEM accumulator
+// and commits them to an mbarrier, and the CTA waits for it (bounded, 1 s of
+// GPU time) before the next chunk. Warps 0..3 then read rows 32w..32w+31
+// from TMEM lanes with tcgen05.ld, add the bias and store. A wait that runs
+// out sets bit 0 of *err; the tile then stores nothing.
+constexpr int kTcRows = 128, kTcCols = 256, kTcKc = 32;
 template <bool TA, bool TB, typename TBv>
-__global__ void __launch_bounds__(kThreads) k_gemm(int M, int N, int k0, int k1, const float* __restrict__ A, int lda,
-                                                   const TBv* __restrict__ B, int ldb, const float* __restrict__ bias,
-                                                   float* __restrict__ C, int ldc) {
-    __shared__ float As[kTileK][kTile + 4];
-    __shared__ float Bs[kTileK][kTile + 4];
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    const int m0 = blockIdx.y * kTile, n0 = blockIdx.x * kTile;
-    float acc[4][4] = {};
-    for (int kb = k0; kb < k1; kb += kTileK) {
-        for (int e = threadIdx.x; e < kTileK * kTile; e += kThreads) {
-            const int kk = e / kTile, mm = e % kTile;
-            const int k = kb + kk, m = m0 + mm;
-            float v = 0.f;
-            if (k < k1 && m < M) v = TA ? A[(int64_t)k * lda + m] : A[(int64_t)m * lda + k];
-            As[kk][mm] = v;
-            const int n = n0 + mm;
-            float w = 0.f;
-            if (k < k1 && n < N) w = (float)(TB ? B[(int64_t)n * ldb + k] : B[(int64_t)k * ldb + n]);
-            Bs[kk][mm] = w;
-        }
-        __syncthreads();
+__global__ void __launch_bounds__(128) k_tc_gemm(int M, int N, int k0, int k1, const float* __restrict__ A, int lda,
+                                                 const TBv* __restrict__ B, int ldb, const float* __restrict__ bias,
+                                                 float* __restrict__ C, int ldc, unsigned* err) {
+    using namespace als;
+    constexpr bool BSPLIT = !std::is_same<TBv, __nv_bfloat16>::value;  // FP32 B: hi and lo parts
+    constexpr int A_BYTES = kTcRows * kTcKc * 4, B_BYTES = kTcCols * kTcKc * 4;
+    extern __shared__ __align__(1024) uint8_t smem_t[];
+    uint8_t* Ah = smem_t;
+    uint8_t* Al = Ah + A_BYTES;
+    uint8_t* Bh = Al + A_BYTES;
+    uint8_t* Bl = Bh + B_BYTES;
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * kTcRows, n0 = blockIdx.y * kTcCols;
+    const int nt = min(kTcCols, (N - n0 + 15) / 16 * 16);  // MMA N: multiple of 16
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                     "r"((uint32_t)kTcCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_slot;
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(nt >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+    // Byte offset of element (row r, k) in an operand tile of R rows (TF32: 4 k per 16-byte core row).
+    auto off = [](int R, int r, int k) { return (uint32_t)((k >> 2) * (R >> 3) * 128 + (r >> 3) * 128 + (r & 7) * 16 + (k & 3) * 4); };
+    uint32_t phase = 0;
+    bool ok = true, first = true;
+    for (int kb = k0; kb < k1; kb += kTcKc) {
+        // A: thread t converts row t of the tile, 32 k.
+        {
+            const int m = m0 + tid;
+            for (int g = 0; g < kTcKc / 4; ++g) {
+                float h4[4], l4[4];
 #pragma unroll
-        for (int kk = 0; kk < kTileK; ++kk) {
-            float a[4], b[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                a[q] = As[kk][ty * 4 + q];
-                b[q] = Bs[kk][tx * 4 + q];
+                for (int q = 0; q < 4; ++q) {
+                    const int k = kb + 4 * g + q;
+                    float x = 0.f;
+                    if (m < M && k < k1) x = TA ? A[(int64_t)k * lda + m] : A[(int64_t)m * lda + k];
+                    const float hi = __uint_as_float(tf32_rna(x));
+                    h4[q] = hi;
+                    l4[q] = __uint_as_float(tf32_rna(x - hi));
+                }
+                *reinterpret_cast<float4*>(Ah + off(kTcRows, tid, 4 * g)) = make_float4(h4[0], h4[1], h4[2], h4[3]);
+                *reinterpret_cast<float4*>(Al + off(kTcRows, tid, 4 * g)) = make_float4(l4[0], l4[1], l4[2], l4[3]);
             }
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-#pragma unroll
-                for (int t = 0; t < 4; ++t) acc[q][t] = fmaf(a[q], b[t], acc[q][t]);
         }
+        // B: rows n = tid, tid + 128 of the tile, element (n, k) = B(k, n).
+        for (int r = tid; r < nt; r += 128) {
+            const int n = n0 + r;
+            for (int g = 0; g < kTcKc / 4; ++g) {
+                float h4[4], l4[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int k = kb + 4 * g + q;
+                    float x = 0.f;
+                    if (n < N && k < k1) x = (float)(TB ? B[(int64_t)n * ldb + k] : B[(int64_t)k * ldb + n]);
+                    const float hi = __uint_as_float(tf32_rna(x));
+                    h4[q] = hi;
+                    l4[q] = __uint_as_float(tf32_rna(x - hi));
+                }
+                *reinterpret_cast<float4*>(Bh + off(nt, r, 4 * g)) = make_float4(h4[0], h4[1], h4[2], h4[3]);
+                if (BSPLIT)
+                    *reinterpret_cast<float4*>(Bl + off(nt, r, 4 * g)) = make_float4(l4[0], l4[1], l4[2], l4[3]);
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-    }
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int m = m0 + ty * 4 + q;
-        if (m >= M) continue;
+            for (int ks = 0; ks < kTcKc / 8; ++ks) {
+                const uint32_t ka = (uint32_t)(2 * ks) * (kTcRows / 8) * 128, kbo = (uint32_t)(2 * ks) * (nt / 8) * 128;
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int n = n0 + tx * 4 + t;
-            if (n < N) C[(int64_t)m * ldc + n] = acc[q][t] + (bias ? bias[n] : 0.f);
+                for (int t = 0; t < (BSPLIT ? 3 : 2); ++t) {
+                    const uint8_t* Ap = t == 1 ? Al : Ah;
+                    const uint8_t* Bp = t == 2 ? Bl : Bh;
+                    const uint64_t ad = umma_desc(smem_addr(Ap) + ka, (kTcRows / 8) * 128, 128);
+                    const uint64_t bd = umma_desc(smem_addr(Bp) + kbo, (uint32_t)(nt / 8) * 128, 128);
+                    const uint32_t accum = (first && ks == 0 && t == 0) ? 0u : 1u;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_addr(&bar)));
         }
+        first = false;
+        // The next chunk overwrites the operands: wait for these MMAs.
+        const bool done = mbar_wait(&bar, phase);
+        if (done) phase ^= 1u;
+        ok = __syncthreads_and(done) != 0;
+        if (!ok) break;
     }
+    if (!ok) {
+        if (tid == 0) report_timeout(err);
+        mbar_wait(&bar, phase);  // one more bounded wait before the accumulator is freed
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (ok && !first) {
+        const int m = m0 + 32 * warp + lane;
+        for (int c0 = 0; c0 < nt; c0 += 16) {
+            uint32_t v[16];
+            const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            if (m < M) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int n = n0 + c0 + j;
+                    if (n < N) C[(int64_t)m * ldc + n] = __uint_as_float(v[j]) + (bias ? bias[n] : 0.f);
+                }
+            }
+        }
+    } else if (ok && first) {  // empty k range: C = bias
+        const int m = m0 + tid;
+        if (m < M)
+            for (int n = n0; n < min(N, n0 + kTcCols); ++n) C[(int64_t)m * ldc + n] = bias ? bias[n] : 0.f;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)kTcCols));
+}
+
+template <bool TA, bool TB, typename TBv>
+void tc_gemm(cudaStream_t st, int M, int N, int k0, int k1, const float* A, int lda, const TBv* B, int ldb,
+             const float* bias, float* C, int ldc, unsigned* err) {
+    if (M <= 0 || N <= 0) return;
+    constexpr size_t smem = 2 * (size_t)kTcRows * kTcKc * 4 + 2 * (size_t)kTcCols * kTcKc * 4;
+    cudaFuncSetAttribute(k_tc_gemm<TA, TB, TBv>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const dim3 grid((M + kTcRows - 1) / kTcRows, (N + kTcCols - 1) / kTcCols);
+    k_tc_gemm<TA, TB, TBv><<<grid, 128, smem, st>>>(M, N, k0, k1, A, lda, B, ldb, bias, C, ldc, err);
 }
 
 __global__ void k_gelu_inplace(float* __restrict__ H, const float* __restrict__ Z, int64_t n) {
@@ -213,8 +327,9 @@ __global__ void k_features(const int64_t* __restrict__ indptr, const int32_t* __
     }
 }
 
-dim3 gemm_grid(int M, int N) { return dim3((N + kTile - 1) / kTile, (M + kTile - 1) / kTile); }
 int blocks_for(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 4096); }
+
+
 
 }  // namespace
 
@@ -234,6 +349,7 @@ struct als_mlp {
           *d2 = nullptr, *part = nullptr;
     double* dpart = nullptr;
     double* loss = nullptr;
+    unsigned* err = nullptr;       // bit 0: a bounded tensor-core wait ran out
     int64_t part_cap = 0;
 
     int64_t oW1() const { return 0; }
@@ -245,6 +361,16 @@ struct als_mlp {
 };
 
 namespace {
+
+int mlp_check(als_mlp* n) {
+    unsigned e = 0;
+    if (cudaMemcpyAsync(&e, n->err, 4, cudaMemcpyDeviceToHost, n->stream) != cudaSuccess ||
+        cudaStreamSynchronize(n->stream) != cudaSuccess)
+        return ALS_ERR_CUDA;
+    if (e == 0) return ALS_OK;
+    cudaMemsetAsync(n->err, 0, 4, n->stream);
+    return ALS_ERR_TIMEOUT;
+}
 
 void mlp_free_work(als_mlp* n) {
     for (float* p : {n->z1, n->h1, n->z2, n->h2, n->y, n->dy, n->d1, n->d2, n->part})
@@ -288,14 +414,14 @@ int forward(als_mlp* n, int64_t rows, const float* X) {
     const int I = n->in, H = n->hid, O = n->out;
     cudaStream_t st = n->stream;
     const __nv_bfloat16* W = n->wb;
-    k_gemm<false, true, __nv_bfloat16><<<gemm_grid((int)rows, H), kThreads, 0, st>>>(
-        (int)rows, H, 0, I, X, I, W + n->oW1(), I, n->w + n->ob1(), n->z1, H);
+    tc_gemm<false, true, __nv_bfloat16>(st, (int)rows, H, 0, I, X, I, W + n->oW1(), I, n->w + n->ob1(), n->z1, H,
+                                        n->err);
     k_gelu_inplace<<<blocks_for(rows * H), 256, 0, st>>>(n->h1, n->z1, rows * H);
-    k_gemm<false, true, __nv_bfloat16><<<gemm_grid((int)rows, H), kThreads, 0, st>>>(
-        (int)rows, H, 0, H, n->h1, H, W + n->oW2(), H, n->w + n->ob2(), n->z2, H);
+    tc_gemm<false, true, __nv_bfloat16>(st, (int)rows, H, 0, H, n->h1, H, W + n->oW2(), H, n->w + n->ob2(), n->z2, H,
+                                        n->err);
     k_gelu_inplace<<<blocks_for(rows * H), 256, 0, st>>>(n->h2, n->z2, rows * H);
-    k_gemm<false, true, __nv_bfloat16><<<gemm_grid((int)rows, O), kThreads, 0, st>>>(
-        (int)rows, O, 0, H, n->h2, H, W + n->oW3(), H, n->w + n->ob3(), n->y, O);
+    tc_gemm<false, true, __nv_bfloat16>(st, (int)rows, O, 0, H, n->h2, H, W + n->oW3(), H, n->w + n->ob3(), n->y, O,
+                                        n->err);
     return cudaGetLastError() == cudaSuccess ? ALS_OK : ALS_ERR_CUDA;
 }
 
@@ -307,8 +433,8 @@ int weight_grad(als_mlp* n, int64_t rows, const float* dZ, int NZ, const float* 
     for (int s = 0; s < splits; ++s) {
         const int r0 = s * kSplitRows, r1 = (int)std::min<int64_t>(rows, (int64_t)(s + 1) * kSplitRows);
         // P[s] (NZ x KA) = dZ[r0:r1]^T A[r0:r1]
-        k_gemm<true, false, float><<<gemm_grid(NZ, KA), kThreads, 0, st>>>(
-            NZ, KA, r0, r1, dZ, NZ, A, KA, nullptr, n->part + (int64_t)s * NZ * KA, KA);
+        tc_gemm<true, false, float>(st, NZ, KA, r0, r1, dZ, NZ, A, KA, nullptr, n->part + (int64_t)s * NZ * KA, KA,
+                                    n->err);
     }
     k_sum_splits<<<blocks_for((int64_t)NZ * KA), 256, 0, st>>>(n->part, splits, (int64_t)NZ * KA, n->g + oW);
     // bias: column sums of dZ
@@ -327,13 +453,11 @@ int backward(als_mlp* n, int64_t rows, const float* X, const float* T) {
     int rc = weight_grad(n, rows, n->dy, O, n->h2, H, n->oW3(), n->ob3());
     if (rc) return rc;
     // d h2 = dy W3 -> dz2
-    k_gemm<false, false, __nv_bfloat16><<<gemm_grid((int)rows, H), kThreads, 0, st>>>(
-        (int)rows, H, 0, O, n->dy, O, W + n->oW3(), H, nullptr, n->d2, H);
+    tc_gemm<false, false, __nv_bfloat16>(st, (int)rows, H, 0, O, n->dy, O, W + n->oW3(), H, nullptr, n->d2, H, n->err);
     k_gelu_back<<<blocks_for(rows * H), 256, 0, st>>>(n->d2, n->d2, n->z2, rows * H);
     rc = weight_grad(n, rows, n->d2, H, n->h1, H, n->oW2(), n->ob2());
     if (rc) return rc;
-    k_gemm<false, false, __nv_bfloat16><<<gemm_grid((int)rows, H), kThreads, 0, st>>>(
-        (int)rows, H, 0, H, n->d2, H, W + n->oW2(), H, nullptr, n->d1, H);
+    tc_gemm<false, false, __nv_bfloat16>(st, (int)rows, H, 0, H, n->d2, H, W + n->oW2(), H, nullptr, n->d1, H, n->err);
     k_gelu_back<<<blocks_for(rows * H), 256, 0, st>>>(n->d1, n->d1, n->z1, rows * H);
     return weight_grad(n, rows, n->d1, H, X, I, n->oW1(), n->ob1());
 }
@@ -354,7 +478,8 @@ int als_mlp_create(als_mlp** out, int in_dim, int hidden, int out_dim, uint64_t 
     const size_t b = n->n_params * 4;
     bool ok = cudaMalloc(&n->w, b) == cudaSuccess && cudaMalloc(&n->m, b) == cudaSuccess &&
               cudaMalloc(&n->v, b) == cudaSuccess && cudaMalloc(&n->g, b) == cudaSuccess &&
-              cudaMalloc(&n->wb, n->n_params * 2) == cudaSuccess && cudaMalloc(&n->loss, 8) == cudaSuccess;
+              cudaMalloc(&n->wb, n->n_params * 2) == cudaSuccess && cudaMalloc(&n->loss, 8) == cudaSuccess &&
+              cudaMalloc(&n->err, 4) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         delete n;
@@ -372,6 +497,7 @@ int als_mlp_create(als_mlp** out, int in_dim, int hidden, int out_dim, uint64_t 
     cudaMemcpy(n->w, h.data(), b, cudaMemcpyHostToDevice);
     cudaMemset(n->m, 0, b);
     cudaMemset(n->v, 0, b);
+    cudaMemset(n->err, 0, 4);
     k_to_bf16<<<blocks_for(n->n_params), 256>>>(n->w, n->wb, n->n_params);
     if (cudaDeviceSynchronize() != cudaSuccess) {
         cudaGetLastError();
@@ -385,7 +511,7 @@ int als_mlp_destroy(als_mlp* n) {
     if (!n) return ALS_ERR_ARG;
     cudaStreamSynchronize(n->stream);
     mlp_free_work(n);
-    for (void* p : {(void*)n->w, (void*)n->m, (void*)n->v, (void*)n->g, (void*)n->wb, (void*)n->loss})
+    for (void* p : {(void*)n->w, (void*)n->m, (void*)n->v, (void*)n->g, (void*)n->wb, (void*)n->loss, (void*)n->err})
         if (p) cudaFree(p);
     delete n;
     return ALS_OK;
@@ -408,7 +534,7 @@ int als_mlp_get_params(als_mlp* n, float* params_host) {
     if (!n || !params_host) return ALS_ERR_ARG;
     if (cudaMemcpyAsync(params_host, n->w, n->n_params * 4, cudaMemcpyDeviceToHost, n->stream) != cudaSuccess)
         return ALS_ERR_CUDA;
-    return cudaStreamSynchronize(n->stream) == cudaSuccess ? ALS_OK : ALS_ERR_CUDA;
+    return mlp_check(n);
 }
 
 int als_mlp_forward(als_mlp* n, int64_t rows, const float* X, float* Y) {
@@ -433,7 +559,8 @@ int als_mlp_grad(als_mlp* n, int64_t rows, const float* X, const float* T, float
         return ALS_ERR_CUDA;
     double l = 0.0;
     if (cudaMemcpyAsync(&l, n->loss, 8, cudaMemcpyDeviceToHost, n->stream) != cudaSuccess) return ALS_ERR_CUDA;
-    if (cudaStreamSynchronize(n->stream) != cudaSuccess) return ALS_ERR_CUDA;
+    rc = mlp_check(n);
+    if (rc) return rc;
     if (loss_host) *loss_host = l / ((double)rows * n->out);
     return ALS_OK;
 }
@@ -452,9 +579,9 @@ int als_mlp_train_step(als_mlp* n, int64_t rows, const float* X, const float* T,
     if (cudaGetLastError() != cudaSuccess) return ALS_ERR_CUDA;
     if (loss_host) {
         double l = 0.0;
-        if (cudaMemcpyAsync(&l, n->loss, 8, cudaMemcpyDeviceToHost, n->stream) != cudaSuccess ||
-            cudaStreamSynchronize(n->stream) != cudaSuccess)
-            return ALS_ERR_CUDA;
+        if (cudaMemcpyAsync(&l, n->loss, 8, cudaMemcpyDeviceToHost, n->stream) != cudaSuccess) return ALS_ERR_CUDA;
+        rc = mlp_check(n);
+        if (rc) return rc;
         *loss_host = l / ((double)rows * n->out);
     }
     return ALS_OK;

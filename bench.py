@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--no-sim", action="store_true", help="skip the simulation-design metrics")
     ap.add_argument("--no-probes", action="store_true", help="skip the roofline probes")
     ap.add_argument("--no-warm", action="store_true", help="skip the learned warm-start record")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batch record")
     return ap.parse_args()
 
 
@@ -285,7 +286,7 @@ KERNEL_FAMILIES = ("cta_rows", "warp_rows", "solve_rows", "split_init", "split_h
 # `roofline.traffic` is that sum over the sweep's measured launches). It
 # holds only for the kernel's sources it was taken from: `roofline.traffic`
 # is null once they hash differently.
-TRAFFIC = {"kernel": "cta_rows", "bytes_per_sweep": 295.2e6, "sources_sha256_16": "1bca918151f341d7",
+TRAFFIC = {"kernel": "cta_rows", "bytes_per_sweep": 183.2e6, "sources_sha256_16": "1bca918151f341d7",
            "sources": ("als_device.cuh", "als_rows.cuh", "als_tc.cuh")}
 
 
@@ -662,7 +663,7 @@ def warmstart_arm(args):
     print(json.dumps(warmstart_leg(args.budget)), flush=True)
 
 
-def batch_arm(args):
+def batch_leg(seed=1, budget=None, precision="fp32", steps=5, warmup=2):
     """64 independent completion problems fitted as one batch (one sweep of
     all width groups replayed as a CUDA graph), against fitting them one by
     one. Problem q: t ~ U(0, 1), n_u = 500 * 100^t, n_m = 300 * (100/3)^t,
@@ -671,9 +672,9 @@ def batch_arm(args):
     100k x 20k workload (rank-32 truth), drawn on the device; r = 0.25."""
     import torch
     from paper_2509_18024_gb300 import core_als
-    rng = np.random.default_rng(args.seed)
-    r = args.budget if args.budget is not None else 0.25
-    prec = PRECISIONS[args.precision]
+    rng = np.random.default_rng(seed)
+    r = budget if budget is not None else 0.25
+    prec = PRECISIONS[precision]
     specs, problems = [], []
     for q in range(64):
         t = rng.random()
@@ -689,14 +690,14 @@ def batch_arm(args):
                          torch.as_tensor(synth.init_factor(n_m, f, 4000 + q)).cuda()))
     rows = sum(a + b for a, b, _, _ in specs)
     batch = core_als.CoreBatch(problems, 0.05, r, precision=prec)
-    batch.fit(args.warmup).synchronize()
+    batch.fit(warmup).synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(batch.stream):
         a.record()
-        batch.fit(args.steps)
+        batch.fit(steps)
         b.record()
     batch.synchronize()
-    ms_batch = a.elapsed_time(b) / args.steps
+    ms_batch = a.elapsed_time(b) / steps
     launches = batch.launches_per_sweep
     batch.close()
     # The same problems one by one (a handle per width, sweeps issued in turn).
@@ -710,20 +711,20 @@ def batch_arm(args):
         engines[f].sweep(Ru, Ri, U, M)
     torch.cuda.synchronize()
     a.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         for (Ru, Ri, f, U, M) in problems:
             engines[f].sweep(Ru, Ri, U, M)
     b.record()
     torch.cuda.synchronize()
-    ms_seq = a.elapsed_time(b) / args.steps
+    ms_seq = a.elapsed_time(b) / steps
     by_f = {}
     for n_u, n_m, nnz, f in specs:
         e = by_f.setdefault(f, [0, 0, 0])
         e[0] += 1
         e[1] += n_u + n_m
         e[2] += nnz
-    out = {"metric": METRIC, "value": rows / (ms_batch / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms_batch, "higher_is_better": True, "dtype": args.precision,
+    out = {"metric": METRIC, "value": rows / (ms_batch / 1e3), "unit": UNIT, "n_gpus": 1, "steps": steps,
+           "warmup": warmup, "ms_per_step": ms_batch, "higher_is_better": True, "dtype": precision,
            "data": "synthetic (device-drawn Zipf)",
            "config": {"workload": "batch64: 64 independent problems, 500x300 .. 50kx10k, n_f in {8,16,32,64,128}, "
                                   f"density 0.5-10 %, Zipf 0.9, r={r}", "problems": 64, "row_solves_per_sweep": rows,
@@ -732,7 +733,13 @@ def batch_arm(args):
            "batched_graph": {"ms_per_sweep": ms_batch, "launches_per_sweep": launches},
            "one_by_one": {"ms_per_sweep": ms_seq, "row_solves_per_s": rows / (ms_seq / 1e3)},
            "speedup_of_batching": ms_seq / ms_batch}
-    print(json.dumps(out), flush=True)
+    for e in engines.values():
+        e.close()
+    return out
+
+
+def batch_arm(args):
+    print(json.dumps(batch_leg(args.seed, args.budget, args.precision, args.steps, args.warmup)), flush=True)
 
 
 def capture_arm(args):
@@ -828,6 +835,8 @@ def main():
                                              f"(est. {t_sweep:.1f} s per sweep)"}
         if world == 1 and not args.no_sim:
             out["simulation_metrics"] = simulation_leg()
+        if world == 1 and not args.no_batch:
+            out["batch64"] = batch_leg(args.seed, None, "fp32", steps=3, warmup=1)
         if world == 1 and not args.no_warm:
             out["warm_start"] = warmstart_leg(train_seeds=(101, 102, 103), held_seeds=(201, 202),
                                               precisions=(0, 2), epochs=12)

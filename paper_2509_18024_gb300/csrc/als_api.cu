@@ -938,21 +938,29 @@ int run_side(als_handle* h, const Plan& pl, const Side& side, int mode, float* X
             const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)h->n_sm * 4));
             ALS_LAUNCH(h, "colmax", als::k_colmax<F><<<blocks, 256, 0, st>>>(side.Y, side.n_cols, p.f, tcol));
         }
+        // At n_f <= 32 a bucket is assembled in pieces of at most kPieceRows
+        // rows, each solved as soon as it is assembled: a piece's systems
+        // (50 MB) are still in L2 when its solve reads them.
+        constexpr int kPieceRows = 12288;
         for (int b = 2; b >= 0; --b) {
             if (pl.n_bucket[b] == 0) continue;
             float* aug = b == 2 ? aug_b2 : (b == 1 ? aug_b1 : aug_b0);
-            rc = launch_cta_bucket<F, ENG>(h, side, p, lists + pl.off_bucket(b),
-                                           pl.blen.data() + (pl.off_bucket(b) - pl.n_warp), pl.n_bucket[b], mode, aug,
-                                           masks_out, tcol);
-            if (rc) return rc;
-            if (overlap && mode == 0) {
-                ALS_CUDA(h, cudaEventRecord(h->ev_bucket[b], st));
-                ALS_CUDA(h, cudaStreamWaitEvent(h->aux3, h->ev_bucket[b], 0));
-                h->stream = h->aux3;
+            const int piece = (F <= 32 && mode == 0) ? kPieceRows : pl.n_bucket[b];
+            for (int a0 = 0; a0 < pl.n_bucket[b]; a0 += piece) {
+                const int cnt = std::min(piece, pl.n_bucket[b] - a0);
+                rc = launch_cta_bucket<F, ENG>(h, side, p, lists + pl.off_bucket(b) + a0,
+                                               pl.blen.data() + (pl.off_bucket(b) - pl.n_warp) + a0, cnt, mode,
+                                               aug + (size_t)a0 * FF, masks_out, tcol);
+                if (rc) return rc;
+                if (overlap && mode == 0) {
+                    ALS_CUDA(h, cudaEventRecord(h->ev_bucket[b], st));
+                    ALS_CUDA(h, cudaStreamWaitEvent(h->aux3, h->ev_bucket[b], 0));
+                    h->stream = h->aux3;
+                }
+                rc = solve_range(pl.off_bucket(b) + a0, cnt);
+                h->stream = st;
+                if (rc) return rc;
             }
-            rc = solve_range(pl.off_bucket(b), pl.n_bucket[b]);
-            h->stream = st;
-            if (rc) return rc;
         }
         if (overlap && mode == 0) {
             ALS_CUDA(h, cudaEventRecord(h->ev_join3, h->aux3));

@@ -526,14 +526,14 @@ int ensure_aux(als_handle* h) {
 // Launch shape of a kernel that may hold tensor memory: CUDA-core engines
 // get one CTA per work item; tensor-core engines a persistent grid whose
 // shared-memory request is padded so that the CTAs resident on one SM never
-// need more than its 512 TMEM columns (two accumulators each).
+// need more than its 512 TMEM columns (one accumulator each).
 template <class K>
 int tc_launch_shape(als_handle* h, K kernel, size_t smem, int eng, uint32_t tmem_cols, int count, int mode,
                     size_t* smem_out, int* grid_out) {
     *smem_out = smem;
     *grid_out = count;
     if (eng == als::ENG_CUDA || mode == 2 || count == 0) return ALS_OK;
-    const int limit = std::max(1, (int)(512 / (2 * tmem_cols)));
+    const int limit = std::max(1, (int)(512 / (als::kTcAccums * tmem_cols)));
     const size_t per_sm = 233472;   // shared memory of one SM
     const size_t reserved = 1024;   // per-CTA reservation
     const size_t floor_smem = per_sm / (limit + 1) - reserved + 1;
@@ -560,9 +560,10 @@ int launch_cta_bucket(als_handle* h, const Side& side, const Params& p, const in
     auto kern = als::k_cta_rows<F, ENG>;
     cudaFuncAttributes fa;
     ALS_CUDA(h, cudaFuncGetAttributes(&fa, kern));
-    // Tensor-core engines hold TMEM: at most 512 / (2 accumulators) columns' worth of CTAs per SM.
-    const int limit =
-        ENG == als::ENG_CUDA ? 64 : std::max(1, (int)(512 / (2 * als::TcCfg<F, als::tc_prec(ENG)>::TMEM_COLS)));
+    // Tensor-core engines hold TMEM: at most 512 columns' worth of accumulators per SM.
+    const int limit = ENG == als::ENG_CUDA
+                          ? 64
+                          : std::max(1, (int)(512 / (als::kTcAccums * als::TcCfg<F, als::tc_prec(ENG)>::TMEM_COLS)));
     auto occ_of = [&](int len) { return std::min(cta_occupancy(fa, L::bytes(std::max(len, 1))), limit); };
     for (int a = 0; a < count;) {
         const int cap = std::max(lens[a], 1);

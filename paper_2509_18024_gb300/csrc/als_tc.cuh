@@ -157,10 +157,14 @@ __device__ __forceinline__ void tc_store(const TcCtx& ctx, bool empty, Store sto
 
 // ---------------------------------------------------------------------------
 // Pipelined, persistent form: two operand tile buffers (each with its own
-// completion barrier) and two TMEM accumulators. Converting chunk c + 1 runs
+// completion barrier) and one TMEM accumulator. Converting chunk c + 1 runs
 // while the MMAs of chunk c execute; a buffer is rewritten only after the
 // commit that last read it completed, so no barrier ever runs two phases
-// ahead of its waiter.
+// ahead of its waiter. A row's (or run's) accumulator is read back before
+// the next row's first MMA is issued, after that row has been staged and
+// selected, so one accumulator keeps the overlap and leaves tensor memory
+// for a second CTA per SM.
+constexpr int kTcAccums = 1;
 struct TcPipe {
     uint32_t tmem;    // base of the two accumulators
     uint32_t ph[2];   // parity of the next completion per buffer
@@ -184,7 +188,7 @@ __device__ __forceinline__ void tc_pipe_setup(uint8_t* tiles, uint64_t* bars, ui
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
-                     "r"(2 * C::TMEM_COLS));
+                     "r"(kTcAccums * C::TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     __syncthreads();
@@ -227,7 +231,7 @@ __device__ __forceinline__ void tc_pipe_row(TcPipe& P, uint8_t* tiles, uint64_t*
     const int tid = threadIdx.x;
     constexpr int KC = C::KC;
     constexpr int GROUPS = C::KT / KC;
-    const uint32_t dacc = P.tmem + (uint32_t)acc * C::TMEM_COLS;
+    const uint32_t dacc = P.tmem + (uint32_t)(acc & (kTcAccums - 1)) * C::TMEM_COLS;
     for (int c0 = 0; c0 < n; c0 += C::KT) {
         const int b = P.next;
         P.next ^= 1;
@@ -321,7 +325,7 @@ __device__ __forceinline__ void tc_pipe_finish(TcPipe& P, uint64_t* bars, int ac
     P.ok = __syncthreads_and(P.ok) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;");
     TcCtx ctx;
-    ctx.tmem = P.tmem + (uint32_t)acc * C::TMEM_COLS;
+    ctx.tmem = P.tmem + (uint32_t)(acc & (kTcAccums - 1)) * C::TMEM_COLS;
     ctx.phase = 0;
     ctx.ok = P.ok;
     tc_store<F, PREC>(ctx, empty, store);
@@ -342,7 +346,8 @@ __device__ __forceinline__ void tc_pipe_teardown(TcPipe& P, uint64_t* bars) {
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if ((threadIdx.x >> 5) == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(P.tmem), "r"(2 * C::TMEM_COLS));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(P.tmem),
+                     "r"(kTcAccums * C::TMEM_COLS));
 }
 
 }  // namespace als

@@ -218,3 +218,77 @@ def test_ranking_ties_and_short_lists(core):
     assert (top[0, 3:] == -1).all()
     ho, no, _ = oracle.rank_metrics(top, rel.indptr, rel.indices, 5, 10)
     assert hit == pytest.approx(ho, abs=1e-12) and ndcg == pytest.approx(no, abs=1e-12)
+
+
+# ------------------------------------- the benchmark's full workload, sampled
+@pytest.fixture(scope="module")
+def zipf():
+    return synth.make_workload("zipf_100k")
+
+
+@pytest.mark.parametrize("variant", [dict(sketch="factor"), dict(fixed_keep=16)])
+@pytest.mark.parametrize("side", ["users", "items"])
+def test_variants_full_size_sampled_rows(core, zipf, variant, side):
+    """The 100k x 20k, 10M-entry, n_f = 32 workload: every row on the GPU in
+    the benchmark's launch configuration, a sample of rows (the longest ones
+    included) against the oracle, masks bit-exact on the sample."""
+    f, lam, r = 32, f32(0.05), 0.25
+    if side == "users":
+        csr, Y = zipf.train_rows, synth.init_factor(zipf.n_m, f, 1000)
+    else:
+        csr, Y = zipf.train_cols, synth.init_factor(zipf.n_u, f, 2000)
+    eng = core.CoreALS(f, lam, r, **variant)
+    R = core.DeviceCSR.from_host(csr)
+    Yd = torch.as_tensor(Y).cuda()
+    X = eng.half_sweep(R, Yd).cpu().numpy()
+    masks = eng.select(R, Yd).cpu().numpy().view(np.uint32)
+    L = np.diff(csr.indptr)
+    rng = np.random.default_rng(1)
+    sample = np.unique(np.concatenate([np.argsort(L)[-12:], rng.choice(csr.n_rows, 300, replace=False)]))
+    Y64 = Y.astype(np.float64)
+    Xo, _, _ = oracle.half_sweep(csr.indptr, csr.indices, csr.values, Y64, lam, r, rows=sample, **variant)
+    assert rel_fro(X[sample], Xo[sample]) <= HALF_TOL
+    lens = L[sample]
+    sub_ptr = np.zeros(len(sample) + 1, np.int64)
+    np.cumsum(lens, out=sub_ptr[1:])
+    take = np.concatenate([np.arange(csr.indptr[i], csr.indptr[i + 1]) for i in sample])
+    mo = oracle.select_half(sub_ptr, csr.indices[take], Y64, r, **variant)
+    assert np.array_equal(masks[take], mo)
+
+
+def test_objective_and_ranking_full_size(core, zipf):
+    """Eq. (object function) over the 9M training entries, and the ranked
+    lists of 100k users over 20k items (ratings >= 4 of the held-out set as
+    the relevant items, Sec. 6's rule for rating data): the objective equals
+    the oracle's within the FP32-prediction bound, the lists of sampled users
+    bit-exact, and Hit@5 / NDCG@10 of those users equal the oracle's."""
+    f, lam = 32, f32(0.05)
+    rng = np.random.default_rng(5)
+    U = (rng.standard_normal((zipf.n_u, f)) * 0.4).astype(np.float32)
+    M = (rng.standard_normal((zipf.n_m, f)) * 0.4).astype(np.float32)
+    eng = core.CoreALS(f, lam, 0.25)
+    Ru = core.DeviceCSR.from_host(zipf.train_rows)
+    Ri = core.DeviceCSR.from_host(zipf.train_cols)
+    Ud, Md = torch.as_tensor(U).cuda(), torch.as_tensor(M).cuda()
+    obj = eng.objective(Ru, Ri, Ud, Md)
+    assert obj == pytest.approx(oracle.objective(zipf.train_rows, zipf.train_cols, U, M, lam), rel=1e-6)
+    rel = synth.relevant_items(zipf.n_u, zipf.n_m, zipf.test_u, zipf.test_m, zipf.test_r, 4.0)
+    hit, ndcg, n, lists = eng.ranking(Ru, core.DeviceCSR.from_host(rel), Ud, Md, 5, 10, want_lists=True)
+    lists = lists.cpu().numpy()
+    users = np.sort(rng.choice(zipf.n_u, 300, replace=False))
+    ip = zipf.train_rows.indptr
+    sub_ip = np.concatenate([[0], np.cumsum(np.diff(ip)[users])]).astype(np.int64)
+    sub_ix = np.concatenate([zipf.train_rows.indices[ip[u]:ip[u + 1]] for u in users])
+    top = oracle.rank_topk(U[users], M, sub_ip, sub_ix, 10)
+    assert np.array_equal(lists[users], top)
+    rip = rel.indptr
+    sub_rp = np.concatenate([[0], np.cumsum(np.diff(rip)[users])]).astype(np.int64)
+    sub_rx = np.concatenate([rel.indices[rip[u]:rip[u + 1]] for u in users]).astype(np.int32)
+    ho, no, _ = oracle.rank_metrics(lists[users], sub_rp, sub_rx, 5, 10)
+    ho2, no2, _ = oracle.rank_metrics(top, sub_rp, sub_rx, 5, 10)
+    assert (ho, no) == (ho2, no2)
+    assert n == int((np.diff(rip) > 0).sum())
+    # The metrics over all users equal the oracle's on the GPU's lists (whose
+    # sampled rows were just checked).
+    ha, na, nn = oracle.rank_metrics(lists, rel.indptr, rel.indices, 5, 10)
+    assert nn == n and hit == pytest.approx(ha, abs=1e-12) and ndcg == pytest.approx(na, abs=1e-12)

@@ -151,14 +151,17 @@ template <int F>
 __global__ void __launch_bounds__(256, 4) k_solve_rows(const float* __restrict__ G_aug, const int32_t* __restrict__ rows,
                                                     int n_list, Params p, float* __restrict__ X_out,
                                                     int32_t* __restrict__ flags_out, Counters* cnt, Fallback fb) {
-    __shared__ float tile[8][F][F + 1];
+    __shared__ __align__(16) float tile[8][F][F + 1];
+    __shared__ __align__(8) uint64_t bar[8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int w = blockIdx.x * 8 + warp;
     if (w >= n_list) return;
     const float* src = G_aug + (int64_t)w * F * (F + 1);
     float* t = &tile[warp][0][0];  // the tile is contiguous with the same layout
-    for (int e = lane; e < F * (F + 1); e += 32) t[e] = __ldg(src + e);
-    __syncwarp();
+    if (!stage_warp(t, src, F * (F + 1), &bar[warp], p.err)) {
+        for (int e = lane; e < F * (F + 1); e += 32) t[e] = 0.f;  // a copy that never completed
+        __syncwarp();
+    }
     float v[F];
 #pragma unroll
     for (int j = 0; j < F; ++j) v[j] = (lane < F) ? tile[warp][lane][j] : 0.f;
@@ -568,16 +571,23 @@ __global__ void __launch_bounds__(RegSolve<F>::NT, F == 64 ? 8 : 2) k_solve_reg(
     __shared__ float s_dinv[F];
     __shared__ float s_pv[F];
     __shared__ int s_ord[F];
+    __shared__ __align__(8) uint64_t bar_ld;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int w = blockIdx.x;
     if (w >= n_list) return;
     float* src = G_aug + (int64_t)w * F * (F + 1);
-    // Stage coalesced through U, then each thread takes its row.
-    for (int e = tid; e < F * (F + 1); e += F) U[e / (F + 1)][e % (F + 1)] = src[e];
+    // Stage the system (row-major, pitch F + 1) in the U area with one bulk
+    // copy, then each thread takes its row.
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_ld)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     __syncthreads();
+    uint32_t ld_phase = 0u;
+    const bool staged = stage_block(smem_f, src, F * (F + 1), &bar_ld, ld_phase, p.err);
     float r[R];
 #pragma unroll
-    for (int j = 0; j < R; ++j) r[j] = U[tid][j];
+    for (int j = 0; j < R; ++j) r[j] = smem_f[tid * (F + 1) + j];
     __syncthreads();
     const bool pivot = p.gram_mode == GRAM_ASYM;
     bool live = true;
@@ -617,7 +627,7 @@ __global__ void __launch_bounds__(RegSolve<F>::NT, F == 64 ? 8 : 2) k_solve_reg(
         for (int s2 = 0; s2 < S; ++s2) y[s2] = U[lane + 32 * s2][F];
         const int64_t i = rows ? (int64_t)rows[w] : (int64_t)w;
         float* xo = X_out + i * p.f;
-        const bool sing = __shfl_sync(kFull, (int)singular, 0) != 0;
+        const bool sing = __shfl_sync(kFull, (int)singular, 0) != 0 || !staged;
 #pragma unroll
         for (int k = F - 1; k >= 0; --k) {
             const float yk = __shfl_sync(kFull, y[k / 32], k % 32);

@@ -99,6 +99,69 @@ __device__ __forceinline__ void report_timeout(unsigned* err) {
     if (err) atomicOr(err, kDevErrTimeout);
 }
 
+// Stages n floats from global src to shared dst, all threads calling. When
+// both addresses are 16-byte aligned and 4 n is a multiple of 16, thread 0
+// issues one bulk copy (cp.async.bulk, completing on `bar`, a one-arrival
+// barrier whose next phase has parity `phase`) and waits for it with the 1 s
+// bound; otherwise a strided loop copies. Returns false (CTA-uniform) if the
+// wait ran out; that copy then gets one more bounded wait, and bit 0 of err
+// is set.
+__device__ __forceinline__ bool stage_block(float* dst, const float* src, int n, uint64_t* bar, uint32_t& phase,
+                                            unsigned* err) {
+    const bool bulk = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15u) == 0 &&
+                      (n & 3) == 0;
+    bool ok = true;
+    if (!bulk) {
+        for (int e = threadIdx.x; e < n; e += blockDim.x) dst[e] = src[e];
+    } else if (threadIdx.x == 0) {
+        const uint32_t bytes = (uint32_t)n * 4u;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                     : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         smem_addr(dst)),
+                     "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                     : "memory");
+        ok = mbar_wait(bar, phase);
+        if (!ok) {
+            report_timeout(err);
+            (void)mbar_wait(bar, phase);
+        }
+        phase ^= 1u;
+    }
+    return __syncthreads_and(ok) != 0;
+}
+
+// Warp-level form of stage_block for a warp's own system: lane 0 sets up the
+// warp's barrier, issues the bulk copy and waits for it (1 s bound); the
+// strided copy when the addresses or size do not allow a bulk copy. Returns
+// false (warp-uniform) if the wait ran out, after a second bounded wait.
+__device__ __forceinline__ bool stage_warp(float* dst, const float* src, int n, uint64_t* bar, unsigned* err) {
+    const int lane = threadIdx.x & 31;
+    const bool bulk = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15u) == 0 &&
+                      (n & 3) == 0;
+    bool ok = true;
+    if (!bulk) {
+        for (int e = lane; e < n; e += 32) dst[e] = src[e];
+    } else if (lane == 0) {
+        const uint32_t bytes = (uint32_t)n * 4u;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                     : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         smem_addr(dst)),
+                     "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                     : "memory");
+        ok = mbar_wait(bar, 0u);
+        if (!ok) {
+            report_timeout(err);
+            (void)mbar_wait(bar, 0u);
+        }
+    }
+    __syncwarp();
+    return __all_sync(0xffffffffu, ok) != 0;
+}
+
 // Self-test of the bounded wait: thread 0 waits on a fresh barrier that
 // nothing arrives at, so the wait runs out after limit_ns and is recorded in
 // the error word exactly as a timeout of the tensor-core pipelines is.

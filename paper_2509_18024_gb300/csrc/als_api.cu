@@ -792,10 +792,10 @@ int launch_solve(als_handle* h, float* aug, const int32_t* list, int count, cons
         ALS_LAUNCH(h, "solve_rows", als::k_solve_rows<F><<<(count + 7) / 8, 256, 0, h->stream>>>(
                                         aug, list, count, p, X_out, flags_out, cnt, fb));
     } else if (replay) {
-        using C = als::BigSolve<F>;
-        ALS_CUDA(h, cudaFuncSetAttribute(als::k_solve_big<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
-        ALS_LAUNCH(h, "solve_rows", als::k_solve_big<F><<<count, C::NT, C::SMEM, h->stream>>>(
-                                        aug, list, count, p, X_out, flags_out, cnt, fb, perm_buf, 0, 1));
+        const size_t smem = (size_t)F * (F + 1) * sizeof(float);
+        ALS_CUDA(h, cudaFuncSetAttribute(als::k_solve_replay<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        ALS_LAUNCH(h, "solve_rows", als::k_solve_replay<F><<<count, 32, smem, h->stream>>>(aug, list, count, p, X_out,
+                                                                                         perm_buf));
     } else {
         using C = als::RegSolve<F>;
         ALS_CUDA(h, cudaFuncSetAttribute(als::k_solve_reg<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));

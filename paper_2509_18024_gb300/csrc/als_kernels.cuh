@@ -261,184 +261,55 @@ __device__ __forceinline__ int cta_lu_solve(T (*A)[F + 1], T* xs, int* s_piv, in
     return flags;
 }
 
-// Batched solve for widths above 32 (F = 64, 128): one CTA per system held in
-// shared memory (row pitch F + 4 floats, rhs in column F). LU with partial
-// pivoting through a row permutation (logical row i lives in physical row
-// perm[i]; nothing moves): at step k the pivot is the largest |a_ik| over
-// logical rows i >= k (lowest i on ties), the multipliers replace column k of
-// the rows below (L), and the trailing update runs over float4 chunks, warps
-// over rows and lanes over chunks. The symmetric modes take the diagonal
-// pivots (Cholesky-equivalent, pivots L_kk^2). One warp then back-substitutes
-// with the unknowns' rows in registers. Same flags and pivot ratio as
-// k_solve_rows.
-//   store != 0: the factored system (L below, U on and above the diagonal,
-//     transformed rhs in column F) goes back to G_aug and the permutation to
-//     perm_buf, for later corrections.
-//   replay != 0: G_aug holds stored factors with a new rhs in column F
-//     (physical row order) and perm_buf their permutation: forward and back
-//     substitution only (the correction of a refinement step).
+// Correction solve of a refinement step at F = 64, 128: forward and back
+// substitution with the factors a previous solve stored (row i of the block:
+// multipliers before its own pivot step, U from it on; the new rhs in column
+// F, physical row order; perm_buf: the physical row of each step). One warp
+// per system: the block (pitch F + 1) comes into shared memory with one bulk
+// copy, lane holds logical rows lane + 32 s; the forward pass takes the
+// steps in order and the back pass in reverse. A bulk copy whose bounded wait ran out
+// leaves a zero correction (and bit 0 of the error word).
 template <int F>
-struct BigSolve {
-    static constexpr int NT = F == 64 ? 128 : 256;  // threads per system
-    static constexpr int P = F + 4;                 // row pitch (floats), 16-byte aligned rows
-    static constexpr int LPR = F / 4;               // lanes per row in the trailing update (one float4 each)
-    static constexpr int RPW = 32 / LPR;            // rows per warp and iteration
-    static constexpr int S = F / 32;                // logical rows per lane in the substitutions
-    static constexpr size_t SMEM = (size_t)F * P * sizeof(float) + F * sizeof(int) + F * sizeof(float) + 16;
-};
-
-template <int F>
-__global__ void __launch_bounds__(BigSolve<F>::NT) k_solve_big(float* __restrict__ G_aug,
-                                                               const int32_t* __restrict__ rows, int n_list,
-                                                               Params p, float* __restrict__ X_out,
-                                                               int32_t* __restrict__ flags_out, Counters* cnt,
-                                                               Fallback fb, int32_t* __restrict__ perm_buf,
-                                                               int store, int replay) {
-    using C = BigSolve<F>;
-    constexpr int NT = C::NT, NW = NT / 32, P = C::P, S = C::S;
-    extern __shared__ __align__(16) float smem_f[];
-    float (*A)[P] = reinterpret_cast<float (*)[P]>(smem_f);
-    int* perm = reinterpret_cast<int*>(smem_f + F * P);
-    float* dinv = reinterpret_cast<float*>(perm + F);  // reciprocals of the pivots (0: zero pivot)
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+__global__ void __launch_bounds__(32) k_solve_replay(const float* __restrict__ G_aug,
+                                                     const int32_t* __restrict__ rows, int n_list, Params p,
+                                                     float* __restrict__ X_out,
+                                                     const int32_t* __restrict__ perm_buf) {
+    constexpr int S = F / 32;
+    extern __shared__ __align__(16) float smem_f[];  // F x (F + 1)
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ float dinv[F];
+    const int lane = threadIdx.x;
     const int w = blockIdx.x;
     if (w >= n_list) return;
-    float* src = G_aug + (int64_t)w * F * (F + 1);
-    for (int a = warp; a < F; a += NW)
-        for (int c = lane; c <= F; c += 32) A[a][c] = src[a * (F + 1) + c];
-    for (int a = tid; a < F; a += NT) {
-        A[a][F + 1] = 0.f;
-        A[a][F + 2] = 0.f;
-        A[a][F + 3] = 0.f;
-        perm[a] = replay ? perm_buf[(int64_t)w * F + a] : a;
+    const bool staged = stage_warp(smem_f, G_aug + (int64_t)w * F * (F + 1), F * (F + 1), &bar, p.err);
+    int pr[S];
+    float y[S];
+#pragma unroll
+    for (int s2 = 0; s2 < S; ++s2) {
+        pr[s2] = min(max(perm_buf[(int64_t)w * F + lane + 32 * s2], 0), F - 1);
+        y[s2] = smem_f[pr[s2] * (F + 1) + F];
+        const float ukk = smem_f[pr[s2] * (F + 1) + lane + 32 * s2];
+        dinv[lane + 32 * s2] = ukk != 0.f ? 1.0f / ukk : 0.f;
     }
-    __syncthreads();
-    const bool pivot = p.gram_mode == GRAM_ASYM;
-    float pmax = 0.f, pmin = __int_as_float(0x7f800000);
-    bool singular = false;
-    if (!replay) {
-        __shared__ int s_pk;
-        for (int k = 0; k < F; ++k) {
-            if (warp == 0) {
-                int bi = k;
-                if (pivot) {
-                    uint32_t bk = 0u;
-                    int bidx = F;
-                    for (int i = k + lane; i < F; i += 32) {
-                        const uint32_t key = __float_as_uint(fabsf(A[perm[i]][k])) + 1u;
-                        if (key > bk) {
-                            bk = key;
-                            bidx = i;
-                        }
-                    }
-                    const uint32_t m = __reduce_max_sync(kFull, bk);
-                    bi = (int)__reduce_min_sync(kFull, (bk == m && m != 0u) ? (uint32_t)bidx : (uint32_t)F);
-                    if (bi >= F) bi = k;
-                }
-                if (lane == 0) {
-                    const int t = perm[k];
-                    perm[k] = perm[bi];
-                    perm[bi] = t;
-                    s_pk = perm[k];
-                    const float pv = A[perm[k]][k];
-                    dinv[k] = pv != 0.f ? 1.0f / pv : 0.f;  // 0 marks a zero pivot
-                    if (k < p.f) {
-                        const float apv = pivot ? fabsf(pv) : pv;
-                        if (!(apv > 0.f)) singular = true;
-                        pmax = fmaxf(pmax, apv);
-                        pmin = fminf(pmin, apv);
-                    }
-                }
-            }
-            __syncthreads();
-            const int pk = s_pk;
-            const float rinv = dinv[k];
-            if (rinv != 0.f)
-                for (int i = k + 1 + tid; i < F; i += NT) A[perm[i]][k] *= rinv;
-            __syncthreads();
-            if (rinv != 0.f) {
-                const int q = lane % C::LPR, sub = lane / C::LPR;
-                if (4 * q + 3 > k) {
-                    float4 u = *reinterpret_cast<const float4*>(&A[pk][4 * q]);
-                    if (4 * q <= k) u.x = 0.f;  // columns <= k hold L or are done
-                    if (4 * q + 1 <= k) u.y = 0.f;
-                    if (4 * q + 2 <= k) u.z = 0.f;
-                    const float ur = A[pk][F];
-                    for (int i = k + 1 + warp * C::RPW + sub; i < F; i += NW * C::RPW) {
-                        const int pi = perm[i];
-                        const float l = A[pi][k];
-                        float4* row = reinterpret_cast<float4*>(&A[pi][4 * q]);
-                        float4 a = *row;
-                        a.x = fmaf(-l, u.x, a.x);
-                        a.y = fmaf(-l, u.y, a.y);
-                        a.z = fmaf(-l, u.z, a.z);
-                        a.w = fmaf(-l, u.w, a.w);
-                        *row = a;
-                        if (q == C::LPR - 1) A[pi][F] = fmaf(-l, ur, A[pi][F]);
-                    }
-                }
-            }
-            __syncthreads();
-        }
+    __syncwarp();
+    // Forward: y_i -= l_ik y_k for logical i > k (unit lower factor).
+#pragma unroll 4
+    for (int k = 0; k < F; ++k) {
+        const float yk = __shfl_sync(kFull, y[k / 32], k % 32);
+#pragma unroll
+        for (int s2 = 0; s2 < S; ++s2)
+            if (lane + 32 * s2 > k) y[s2] = fmaf(-smem_f[pr[s2] * (F + 1) + k], yk, y[s2]);
     }
-    // Substitutions by warp 0: lane holds logical rows lane + 32 s.
-    if (warp == 0) {
-        int pr[S];
-        float y[S];
+    const int64_t i = rows ? (int64_t)rows[w] : (int64_t)w;
+    float* xo = X_out + i * p.f;
+#pragma unroll 4
+    for (int k = F - 1; k >= 0; --k) {
+        const float yk = __shfl_sync(kFull, y[k / 32], k % 32);
+        const float xk = yk * dinv[k];
+        if (lane == k % 32 && k < p.f) xo[k] = staged ? xk : 0.f;
 #pragma unroll
-        for (int s2 = 0; s2 < S; ++s2) {
-            pr[s2] = perm[lane + 32 * s2];
-            y[s2] = A[pr[s2]][F];
-        }
-        if (replay) {
-            // Forward: y_i -= l_ik y_k for logical i > k (unit lower factor).
-#pragma unroll
-            for (int k = 0; k < F; ++k) {
-                const float yk = __shfl_sync(kFull, y[k / 32], k % 32);
-#pragma unroll
-                for (int s2 = 0; s2 < S; ++s2)
-                    if (lane + 32 * s2 > k) y[s2] = fmaf(-A[pr[s2]][k], yk, y[s2]);
-            }
-        }
-        const int64_t i = rows ? (int64_t)rows[w] : (int64_t)w;
-        float* xo = X_out + i * p.f;
-        const bool sing = __shfl_sync(kFull, (int)singular, 0) != 0;  // tid 0 kept the statistics
-        if (replay)
-            for (int k = lane; k < F; k += 32) {
-                const float ukk = A[perm[k]][k];
-                dinv[k] = ukk != 0.f ? 1.0f / ukk : 0.f;
-            }
-        __syncwarp();
-#pragma unroll
-        for (int k = F - 1; k >= 0; --k) {
-            const float yk = __shfl_sync(kFull, y[k / 32], k % 32);
-            const float xk = yk * dinv[k];
-            if (lane == k % 32 && k < p.f) xo[k] = sing ? 0.f : xk;
-#pragma unroll
-            for (int s2 = 0; s2 < S; ++s2)
-                if (lane + 32 * s2 < k) y[s2] = fmaf(-A[pr[s2]][k], xk, y[s2]);
-        }
-    }
-    if (replay) return;
-    if (store) {
-        __syncthreads();
-        for (int a = warp; a < F; a += NW)
-            for (int c = lane; c <= F; c += 32) src[a * (F + 1) + c] = A[a][c];
-        for (int a = tid; a < F; a += NT) perm_buf[(int64_t)w * F + a] = perm[a];
-    }
-    if (tid == 0) {
-        int flags = 0;
-        float ratio = (p.f > 0) ? pmax / pmin : 1.f;
-        if (singular) {
-            flags = FLAG_SINGULAR | FLAG_RATIO;
-            ratio = __int_as_float(0x7f800000);
-        } else if (!(ratio <= p.ratio_max)) {
-            flags = FLAG_RATIO;
-        }
-        const int64_t i = rows ? (int64_t)rows[w] : (int64_t)w;
-        if (flags_out) flags_out[i] = flags;
-        record_flags(cnt, flags, ratio);
-        fallback_push(fb, flags, i);
+        for (int s2 = 0; s2 < S; ++s2)
+            if (lane + 32 * s2 < k) y[s2] = fmaf(-smem_f[pr[s2] * (F + 1) + k], xk, y[s2]);
     }
 }
 
@@ -451,10 +322,11 @@ __global__ void __launch_bounds__(BigSolve<F>::NT) k_solve_big(float* __restrict
 // on ties; row k itself for the symmetric modes), its row is published as
 // float4s into U[k] (shared memory, U in step order), and every live row
 // subtracts l_ik U[k] with l_ik = a_ik / u_kk, keeping l_ik in the dead
-// register. One warp back-substitutes from U. Same pivots, products and
-// rounding as k_solve_big. store != 0: each row's block of L / U entries goes
-// back to G_aug (L before the row's own pivot step, U from it on) and the
-// physical row of each step to perm_buf, as k_solve_big stores them.
+// register. One warp back-substitutes from U. Rows never move (partial
+// pivoting through the step order). store != 0: each row's block of L / U
+// entries goes back to G_aug (L before the row's own pivot step, U from it
+// on) and the physical row of each step to perm_buf, the form k_solve_replay
+// reads.
 template <int F>
 struct RegSolve {
     static constexpr int NT = F;      // threads per system

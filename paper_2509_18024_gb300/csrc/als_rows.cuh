@@ -623,7 +623,7 @@ struct CtaLayout {
 // tiles are set up once per CTA, and each row's accumulator is read back
 // after the next row has been staged and selected (its MMAs run meanwhile).
 template <int F, int ENG>
-__global__ void __launch_bounds__(kCtaThreads, ENG == ENG_CUDA ? 4 : 1) k_cta_rows(Side side, Params p, const int32_t* __restrict__ rows,
+__global__ void __launch_bounds__(kCtaThreads, ENG == ENG_CUDA ? 4 : 2) k_cta_rows(Side side, Params p, const int32_t* __restrict__ rows,
                                                           int n_list, int cap, int mode, float* __restrict__ G_aug,
                                                           uint32_t* __restrict__ masks_out,
                                                           const uint32_t* __restrict__ tcol) {
@@ -672,10 +672,19 @@ __global__ void __launch_bounds__(kCtaThreads, ENG == ENG_CUDA ? 4 : 1) k_cta_ro
             if (prev_w < 0) return;
             float* dst = G_aug + (int64_t)prev_w * F * (F + 1);
             const float reg = prev_reg;
-            tc_pipe_finish<F, PREC>(P, s_bars, prev_acc, prev_n == 0, [&](int a, int c, float v) {
-                if (a == c) v = (a < f) ? v + reg : 1.f;
-                dst[a * (F + 1) + c] = v;
-            });
+            // The selection bins are free here (every warp has selected this
+            // row's columns): they carry the transpose, then are cleared.
+            static_assert(L::HIST_BYTES >= kTcStoreBufFloats * 4, "transpose buffer in the bins");
+            tc_pipe_finish<F, PREC>(
+                P, s_bars, prev_acc, prev_n == 0,
+                [&](int a, int c, float v) {
+                    if (a == c) v = (a < f) ? v + reg : 1.f;
+                    dst[a * (F + 1) + c] = v;
+                },
+                reinterpret_cast<float*>(s_u));
+            __syncthreads();
+            for (int e = tid; e < (int)(L::HIST_BYTES / 16); e += kCtaThreads)
+                reinterpret_cast<uint4*>(s_u)[e] = make_uint4(0u, 0u, 0u, 0u);
             prev_w = -1;
         }
     };
@@ -1003,7 +1012,9 @@ struct SplitGramSmem {
     float r[CH];
     int32_t idx[CH];
     uint32_t mask[CH][W];
-    __align__(1024) uint8_t u[ENG == ENG_CUDA ? kGramBufs * F * (F + 1) * 4 : 16];
+    // CUDA cores: the warps' Gram partials; tensor cores: the transpose
+    // buffer of the accumulator read-back.
+    __align__(1024) uint8_t u[ENG == ENG_CUDA ? kGramBufs * F * (F + 1) * 4 : kTcStoreBufFloats * 4];
     __align__(1024) uint8_t tiles[TileBytes<F, ENG>::value];
     uint64_t bars[2];
     uint32_t tmem_slot;
@@ -1037,8 +1048,9 @@ __global__ void __launch_bounds__(kCtaThreads) k_split_gram(Side side, Params p,
         if constexpr (TC) {
             if (prev_c < 0) return;
             float* dst = st.part + (int64_t)prev_c * F * (F + 1);
-            tc_pipe_finish<F, PREC>(P, S.bars, prev_acc, prev_len == 0,
-                                    [&](int a, int cc, float v) { dst[a * (F + 1) + cc] = v; });
+            tc_pipe_finish<F, PREC>(
+                P, S.bars, prev_acc, prev_len == 0, [&](int a, int cc, float v) { dst[a * (F + 1) + cc] = v; },
+                reinterpret_cast<float*>(S.u));
             prev_c = -1;
         }
     };

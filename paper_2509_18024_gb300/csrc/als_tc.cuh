@@ -218,6 +218,41 @@ __device__ __forceinline__ void tc_store(const TcCtx& ctx, bool empty, Store sto
     }
 }
 
+// Floats of the transpose buffer tc_store_rows needs (32 x 17 per warp, warps 0..3).
+constexpr int kTcStoreBufFloats = 4 * 32 * 17;
+
+// Same values as tc_store, handed to store(a, c, v) in an order where the
+// lanes of a warp take 16 consecutive columns of two rows: each warp passes
+// its 32 x 16 block through a 32 x 17 transpose buffer (tbuf, warp w at
+// w * 32 * 17), so that stores into a row-major [F][F + 1] block coalesce.
+template <int F, int PREC, class Store>
+__device__ __forceinline__ void tc_store_rows(const TcCtx& ctx, bool empty, Store store, float* tbuf) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp >= 4 || 32 * warp >= F) return;
+    float* T = tbuf + warp * 32 * 17;
+#pragma unroll 1
+    for (int c0 = 0; c0 <= F; c0 += 16) {
+        uint32_t v[16];
+        const uint32_t taddr = ctx.tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+        for (int j = 0; j < 16; ++j) T[lane * 17 + j] = (empty || !ctx.ok) ? 0.f : __uint_as_float(v[j]);
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int rr = 2 * i + (lane >> 4), jj = lane & 15;
+            const int a = 32 * warp + rr, c = c0 + jj;
+            if (a < F && c <= F) store(a, c, T[rr * 17 + jj]);
+        }
+        __syncwarp();
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Pipelined, persistent form: two operand tile buffers (each with its own
 // completion barrier) and one TMEM accumulator. Converting chunk c + 1 runs
@@ -379,9 +414,12 @@ __device__ __forceinline__ void tc_pipe_row(TcPipe& P, uint8_t* tiles, uint64_t*
 }
 
 // Wait for every outstanding MMA, then read accumulator `acc` (rows 0..F-1,
-// columns 0..F) into store(a, c, v); `empty` rows store zeros.
+// columns 0..F) into store(a, c, v); `empty` rows store zeros. With tbuf
+// (kTcStoreBufFloats of free shared memory) the values go out in the
+// coalescing order of tc_store_rows.
 template <int F, int PREC, class Store>
-__device__ __forceinline__ void tc_pipe_finish(TcPipe& P, uint64_t* bars, int acc, bool empty, Store store) {
+__device__ __forceinline__ void tc_pipe_finish(TcPipe& P, uint64_t* bars, int acc, bool empty, Store store,
+                                               float* tbuf = nullptr) {
     using C = TcCfg<F, PREC>;
     tc_pipe_drain(P, bars, 0);
     tc_pipe_drain(P, bars, 1);
@@ -391,7 +429,10 @@ __device__ __forceinline__ void tc_pipe_finish(TcPipe& P, uint64_t* bars, int ac
     ctx.tmem = P.tmem + (uint32_t)(acc & (kTcAccums - 1)) * C::TMEM_COLS;
     ctx.phase = 0;
     ctx.ok = P.ok;
-    tc_store<F, PREC>(ctx, empty, store);
+    if (tbuf != nullptr)
+        tc_store_rows<F, PREC>(ctx, empty, store, tbuf);
+    else
+        tc_store<F, PREC>(ctx, empty, store);
 }
 
 // Free the accumulators. After a wait that ran out, each commit still marked

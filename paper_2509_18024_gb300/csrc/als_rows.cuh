@@ -38,6 +38,10 @@ template <int F>
 struct SplitHistCols {
     static constexpr int value = F < 32 ? F : 32;
 };
+// Resident CTAs per SM that k_split_gram is compiled for: one for the
+// tensor-core engines (their tiles fill shared memory; without the bound the
+// compiler holds them to 64 registers), two or four on the CUDA cores.
+__host__ __device__ constexpr int split_gram_min_blocks(int F, int eng) { return eng != 0 ? 1 : (F >= 32 ? 2 : 4); }
 __host__ __device__ constexpr int split_hist_cols(int F) { return F < 32 ? F : 32; }
 
 // Mask words per position.
@@ -1029,7 +1033,7 @@ struct SplitGramSmem {
 // cores a run's accumulator is read back while the next run's first chunk is
 // staged and its MMAs run.
 template <int F, int ENG>
-__global__ void __launch_bounds__(kCtaThreads) k_split_gram(Side side, Params p, SplitPlan sp, SplitState st,
+__global__ void __launch_bounds__(kCtaThreads, split_gram_min_blocks(F, ENG)) k_split_gram(Side side, Params p, SplitPlan sp, SplitState st,
                                                             int mode, uint32_t* __restrict__ masks_out, int per) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     using Smem = SplitGramSmem<F, ENG>;

@@ -322,8 +322,12 @@ __global__ void __launch_bounds__(32) k_solve_replay(const float* __restrict__ G
 // on ties; row k itself for the symmetric modes), its row is published as
 // float4s into U[k] (shared memory, U in step order), and every live row
 // subtracts l_ik U[k] with l_ik = a_ik / u_kk, keeping l_ik in the dead
-// register. One warp back-substitutes from U. Rows never move (partial
-// pivoting through the step order). store != 0: each row's block of L / U
+// register. At n_f = 128 a step updates only the block's own 8 columns and
+// the trailing columns take the block's 8 updates together afterwards
+// (reg_lu_block); the results are the same bit for bit, and the deferred
+// form needs 168 registers, so three CTAs share an SM. One warp
+// back-substitutes from U. Rows never move (partial pivoting through the
+// step order). store != 0: each row's block of L / U
 // entries goes back to G_aug (L before the row's own pivot step, U from it
 // on) and the physical row of each step to perm_buf, the form k_solve_replay
 // reads.
@@ -341,8 +345,156 @@ struct RegSolve {
 // 8t + 7 in registers 0..7), then the left shift by 8. NCHB bounds the float4
 // chunks that can still hold live columns in this block (compile-time, so
 // that later blocks skip the dead tail without runtime tests).
+// The steps update only the block's own 8 columns; the trailing columns
+// (and the rhs) take the block's 8 updates afterwards in one pass with no
+// barrier between them. Each pivot row publishes its trailing part as it
+// stands, and a triangular solve with a thread per trailing column (the
+// earlier steps' multiples of the published rows taken off in step order)
+// turns those into the U rows, so every product and its place in each sum
+// are those of eliminating one step at a time.
 template <int F, int NCHB>
 __device__ __forceinline__ void reg_lu_block(float (&r)[F + 1], const int t, bool& live, const bool pivot,
+                                             float (*U)[F + 4], uint32_t (*s_key)[F / 32], int (*s_idx)[F / 32],
+                                             float* s_pv, float* s_dinv, int* s_ord, const int store, float* src) {
+    constexpr int NW = F / 32, R = F + 1;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int rem = R - 8 * t;  // registers still holding columns 8t .. F
+    int own = -1;  // the step of this block at which this row is the pivot
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        const int k = 8 * t + s;
+        uint32_t key;
+        if (pivot) key = live ? __float_as_uint(fabsf(r[s])) + 1u : 0u;
+        else key = tid == k ? 1u : 0u;
+        const uint32_t m = __reduce_max_sync(kFull, key);
+        const unsigned bal = __ballot_sync(kFull, key == m && m != 0u);
+        if (lane == 0) {
+            s_key[k & 1][warp] = m;
+            s_idx[k & 1][warp] = bal ? warp * 32 + __ffs(bal) - 1 : F;
+        }
+        __syncthreads();
+        uint32_t bm = 0u;
+        int pidx = F;
+#pragma unroll
+        for (int v = 0; v < NW; ++v) {
+            const uint32_t kv = s_key[k & 1][v];
+            const int iv = s_idx[k & 1][v];
+            if (kv > bm || (kv == bm && iv < pidx)) {
+                bm = kv;
+                pidx = iv;
+            }
+        }
+        if (tid == pidx) {
+            float* urow = &U[k][8 * t];
+#pragma unroll
+            for (int c = 0; c < NCHB; ++c) {
+                if (4 * c < rem) {
+                    if (4 * c + 3 < R) {
+                        *reinterpret_cast<float4*>(urow + 4 * c) = make_float4(r[4 * c], r[4 * c + 1], r[4 * c + 2], r[4 * c + 3]);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (4 * c + e < R) urow[4 * c + e] = r[4 * c + e];
+                    }
+                }
+            }
+            const float pv = r[s];
+            s_pv[k] = pv;
+            s_dinv[k] = pv != 0.f ? 1.0f / pv : 0.f;
+            s_ord[k] = tid;
+            live = false;
+            own = s;
+        }
+        __syncthreads();
+        const float di = s_dinv[k];
+        if (live && di != 0.f) {
+            const float l = r[s] * di;
+            r[s] = l;
+            const float* urow = &U[k][8 * t];
+#pragma unroll
+            for (int j = s + 1; j < 8; ++j) r[j] = fmaf(-l, urow[j], r[j]);
+        }
+    }
+    // U rows of the block's steps, trailing columns (rhs included): thread
+    // tid takes column 8t + 8 + tid. The published rows read here were all
+    // written before the last step's barrier; the block's own columns, which
+    // the last step's updates read, are not touched.
+    if (8 + tid < rem) {
+        const int col = 8 * t + 8 + tid;
+        float u[8];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) u[s] = U[8 * t + s][col];
+#pragma unroll
+        for (int s = 0; s < 7; ++s) {
+            if (s_dinv[8 * t + s] != 0.f) {
+#pragma unroll
+                for (int s2 = s + 1; s2 < 8; ++s2) u[s2] = fmaf(-U[8 * t + s2][8 * t + s], u[s], u[s2]);
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < 8; ++s) U[8 * t + s][col] = u[s];
+    }
+    __syncthreads();
+    if (live) {
+        // The block's 8 updates of the trailing columns: chunk by chunk, each
+        // element taking the steps in order.
+        float l[8];
+        bool use[8];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            use[s] = s_dinv[8 * t + s] != 0.f;
+            l[s] = r[s];
+        }
+#pragma unroll
+        for (int c = 2; c < NCHB; ++c) {
+            if (4 * c < rem) {
+#pragma unroll
+                for (int s = 0; s < 8; ++s) {
+                    if (!use[s]) continue;
+                    const float* urow = &U[8 * t + s][8 * t];
+                    float u4[4];
+                    if (4 * c + 3 < R) {
+                        const float4 v = *reinterpret_cast<const float4*>(urow + 4 * c);
+                        u4[0] = v.x;
+                        u4[1] = v.y;
+                        u4[2] = v.z;
+                        u4[3] = v.w;
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) u4[e] = (4 * c + e < R) ? urow[4 * c + e] : 0.f;
+                    }
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int j = 4 * c + e;
+                        if (j < R) r[j] = fmaf(-l[s], u4[e], r[j]);
+                    }
+                }
+            }
+        }
+    } else if (store && own >= 0) {
+        // This block's pivot rows take their finished U entries back, so that
+        // the later blocks store them.
+        const float* urow = &U[8 * t + own][8 * t];
+#pragma unroll
+        for (int c = 2; c < NCHB; ++c)
+            if (4 * c < rem)
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (4 * c + e < R) r[4 * c + e] = urow[4 * c + e];
+    }
+    if (store) {
+        float* dst = src + (int64_t)tid * (F + 1) + 8 * t;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) dst[e] = r[e];
+    }
+#pragma unroll
+    for (int j = 0; j + 8 < R; ++j) r[j] = r[j + 8];
+}
+
+// n_f = 64 form of reg_lu_block: every step updates the whole remaining
+// row at once (the deferred trailing update does not pay at this width).
+template <int F, int NCHB>
+__device__ __forceinline__ void reg_lu_steps(float (&r)[F + 1], const int t, bool& live, const bool pivot,
                                              float (*U)[F + 4], uint32_t (*s_key)[F / 32], int (*s_idx)[F / 32],
                                              float* s_pv, float* s_dinv, int* s_ord, const int store, float* src) {
     constexpr int NW = F / 32, R = F + 1;
@@ -431,7 +583,7 @@ __device__ __forceinline__ void reg_lu_block(float (&r)[F + 1], const int t, boo
 }
 
 template <int F>
-__global__ void __launch_bounds__(RegSolve<F>::NT, F == 64 ? 8 : 2) k_solve_reg(
+__global__ void __launch_bounds__(RegSolve<F>::NT, F == 64 ? 8 : 3) k_solve_reg(
     float* __restrict__ G_aug, const int32_t* __restrict__ rows, int n_list, Params p, float* __restrict__ X_out,
     int32_t* __restrict__ flags_out, Counters* cnt, Fallback fb, int32_t* __restrict__ perm_buf, int store) {
     using C = RegSolve<F>;
@@ -469,7 +621,7 @@ __global__ void __launch_bounds__(RegSolve<F>::NT, F == 64 ? 8 : 2) k_solve_reg(
     constexpr int QB = F / 32;  // blocks per quarter
     if constexpr (F < 128) {
         for (int t = 0; t < F / 8; ++t)
-            reg_lu_block<F, (R + 3) / 4>(r, t, live, pivot, U, s_key, s_idx, s_pv, s_dinv, s_ord, store, src);
+            reg_lu_steps<F, (R + 3) / 4>(r, t, live, pivot, U, s_key, s_idx, s_pv, s_dinv, s_ord, store, src);
     } else {
     for (int t = 0; t < QB; ++t)
         reg_lu_block<F, (R + 3) / 4>(r, t, live, pivot, U, s_key, s_idx, s_pv, s_dinv, s_ord, store, src);

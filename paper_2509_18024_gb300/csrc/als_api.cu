@@ -32,7 +32,7 @@ struct BucketCaps {
 BucketCaps bucket_caps(int F) {
     if (F <= 32) return {{128, 512, 1024}};
     if (F == 64) return {{128, 256, 512}};
-    return {{32, 64, 128}};
+    return {{64, 128, 256}};
 }
 
 struct Plan {

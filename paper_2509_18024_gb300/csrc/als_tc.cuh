@@ -316,6 +316,54 @@ __device__ __forceinline__ void tc_pipe_drain(TcPipe& P, uint64_t* bars, int b) 
     }
 }
 
+// One 16-byte group of operand rows: feature m (or the rhs, RHS) at the
+// KC positions of group g of the tile starting at c0. A takes the masked
+// value, B the unmasked one (asymmetric Gram; masked in the symmetric
+// modes; the rhs unmasked), split into TF32 hi and lo in the split mode.
+template <int F, int PREC, int W, bool RHS>
+__device__ __forceinline__ void tc_conv_item(uint8_t* A0, uint8_t* B0, uint8_t* A1, uint8_t* B1,
+                                             const float (*x)[xpitch(F)], const uint32_t (*mask)[W], const float* r,
+                                             int n, bool sym, int c0, int m, int g) {
+    using C = TcCfg<F, PREC>;
+    constexpr int KC = C::KC;
+    float va[8], vb[8], la[8], lb[8];
+#pragma unroll
+    for (int q = 0; q < KC; ++q) {
+        const int k = c0 + g * KC + q;
+        float xv = 0.f, keep = 0.f;
+        if (k < n) {
+            if (!RHS) {
+                xv = x[k][m];
+                keep = ((mask[k][m >> 5] >> (m & 31)) & 1u) ? 1.f : 0.f;
+            } else {
+                xv = r[k];
+                keep = 1.f;
+            }
+        }
+        const float a = keep * xv;
+        const float bv = (!RHS && sym) ? a : xv;
+        if (PREC == TC_TF32X3) {
+            const float ah = __uint_as_float(tf32_rna(a)), bh = __uint_as_float(tf32_rna(bv));
+            va[q] = ah;
+            vb[q] = bh;
+            la[q] = __uint_as_float(tf32_rna(a - ah));
+            lb[q] = __uint_as_float(tf32_rna(bv - bh));
+        } else if (PREC == TC_TF32) {
+            va[q] = __uint_as_float(tf32_rna(a));
+            vb[q] = __uint_as_float(tf32_rna(bv));
+        } else {
+            va[q] = a;
+            vb[q] = bv;
+        }
+    }
+    if (!RHS) put16<PREC>(A0 + C::off(C::M, m, g * KC), va, KC);
+    put16<PREC>(B0 + C::off(C::N, m, g * KC), vb, KC);
+    if (PREC == TC_TF32X3) {
+        if (!RHS) put16<PREC>(A1 + C::off(C::M, m, g * KC), la, KC);
+        put16<PREC>(B1 + C::off(C::N, m, g * KC), lb, KC);
+    }
+}
+
 // Accumulate positions [0, n) of a staged tile into accumulator `acc`
 // (0 or 1), starting it from zero when `fresh` (else adding to what it
 // holds). All threads call it; MMAs stay in flight. Once a wait has run out
@@ -338,44 +386,14 @@ __device__ __forceinline__ void tc_pipe_row(TcPipe& P, uint8_t* tiles, uint64_t*
         uint8_t* B0 = A0 + C::A_BYTES;
         uint8_t* A1 = B0 + C::B_BYTES;
         uint8_t* B1 = A1 + C::A_BYTES;
-        for (int e = tid; P.ok && e < (F + 1) * GROUPS; e += blockDim.x) {
-            const int m = e % (F + 1), g = e / (F + 1);
-            float va[8], vb[8], la[8], lb[8];
-#pragma unroll
-            for (int q = 0; q < KC; ++q) {
-                const int k = c0 + g * KC + q;
-                float xv = 0.f, keep = 0.f;
-                if (k < n) {
-                    if (m < F) {
-                        xv = x[k][m];
-                        keep = ((mask[k][m >> 5] >> (m & 31)) & 1u) ? 1.f : 0.f;
-                    } else {
-                        xv = r[k];
-                        keep = 1.f;
-                    }
-                }
-                const float a = keep * xv;
-                const float bv = (m < F && sym) ? a : xv;
-                if (PREC == TC_TF32X3) {
-                    const float ah = __uint_as_float(tf32_rna(a)), bh = __uint_as_float(tf32_rna(bv));
-                    va[q] = ah;
-                    vb[q] = bh;
-                    la[q] = __uint_as_float(tf32_rna(a - ah));
-                    lb[q] = __uint_as_float(tf32_rna(bv - bh));
-                } else if (PREC == TC_TF32) {
-                    va[q] = __uint_as_float(tf32_rna(a));
-                    vb[q] = __uint_as_float(tf32_rna(bv));
-                } else {
-                    va[q] = a;
-                    vb[q] = bv;
-                }
-            }
-            if (m < F) put16<PREC>(A0 + C::off(C::M, m, g * KC), va, KC);
-            put16<PREC>(B0 + C::off(C::N, m, g * KC), vb, KC);
-            if (PREC == TC_TF32X3) {
-                if (m < F) put16<PREC>(A1 + C::off(C::M, m, g * KC), la, KC);
-                put16<PREC>(B1 + C::off(C::N, m, g * KC), lb, KC);
-            }
+        static_assert((F & (F - 1)) == 0, "tensor-core widths are powers of two");
+        // Feature rows (F a power of two: the index split is a mask and a
+        // shift, and no warp straddles the rhs), then the rhs row of B.
+        if (P.ok) {
+            for (int e = tid; e < F * GROUPS; e += blockDim.x)
+                tc_conv_item<F, PREC, W, false>(A0, B0, A1, B1, x, mask, r, n, sym, c0, e & (F - 1), e / F);
+            for (int g = tid; g < GROUPS; g += blockDim.x)
+                tc_conv_item<F, PREC, W, true>(A0, B0, A1, B1, x, mask, r, n, sym, c0, F, g);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         P.ok = __syncthreads_and(P.ok) != 0;

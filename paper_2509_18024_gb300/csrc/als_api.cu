@@ -772,12 +772,14 @@ int launch_split(als_handle* h, const Plan& pl, const Side& side, const Params& 
     return ALS_OK;
 }
 
-// Warp-per-row CES and Gram of the rows with at most 32 positions (n_f <= 32).
+// Warp-per-row CES and Gram of the rows with at most 32 positions (n_f <= 32);
+// mode 0: each warp also solves its row into X_out; 1: the systems go to aug.
 template <int F>
 int launch_warp_rows(als_handle* h, const Side& side, const Params& p, const int32_t* list, int count, int mode,
-                     uint32_t* masks_out, float* aug) {
+                     uint32_t* masks_out, float* aug, float* X_out, int32_t* flags_out, als::Fallback fb) {
     ALS_LAUNCH(h, "warp_rows", als::k_warp_rows<F><<<(count + 7) / 8, 256, 0, h->stream>>>(
-                                   side, p, list, count, mode == 2, masks_out, aug));
+                                   side, p, list, count, mode == 2, masks_out, aug, mode == 0 ? X_out : nullptr,
+                                   flags_out, counters(h), fb));
     return ALS_OK;
 }
 
@@ -923,8 +925,7 @@ int run_side(als_handle* h, const Plan& pl, const Side& side, int mode, float* X
                 ALS_CUDA(h, cudaStreamWaitEvent(h->aux2, h->ev_fork, 0));
                 h->stream = h->aux2;
             }
-            rc = launch_warp_rows<F>(h, side, p, lists, n_warp, mode, masks_out, aug_warp);
-            if (!rc) rc = solve_range(0, n_warp);
+            rc = launch_warp_rows<F>(h, side, p, lists, n_warp, mode, masks_out, aug_warp, X_out, flags_out, fb);
             h->stream = st;
             if (rc) return rc;
             if (overlap) ALS_CUDA(h, cudaEventRecord(h->ev_join2, h->aux2));

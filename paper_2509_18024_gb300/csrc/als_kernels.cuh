@@ -22,8 +22,10 @@ constexpr int kWarpRowMax = 32;
 
 // ---------------------------------------------------------------------------
 // Warp per row (n_i <= 32): gather, CES and the masked Gram of the row; the
-// augmented system [G | b] (regulariser added, padding rows identity) goes
-// to G_aug[w] for the batched solve. masks_only: stop after the masks.
+// augmented system [G | b] (regulariser added, padding rows identity) is
+// solved by the same warp into X_out (flags, counters and FP64 redo list as
+// k_solve_rows), or, with X_out null, goes to G_aug[w]. masks_only: stop
+// after the masks.
 template <int F>
 struct WarpRowTile {
     union {
@@ -36,9 +38,10 @@ struct WarpRowTile {
 };
 
 template <int F>
-__global__ void __launch_bounds__(256, 4) k_warp_rows(Side side, Params p, const int32_t* __restrict__ rows,
+__global__ void __launch_bounds__(256, 3) k_warp_rows(Side side, Params p, const int32_t* __restrict__ rows,
                                                    int n_list, bool masks_only, uint32_t* __restrict__ masks_out,
-                                                   float* __restrict__ G_aug) {
+                                                   float* __restrict__ G_aug, float* __restrict__ X_out,
+                                                   int32_t* __restrict__ flags_out, Counters* cnt, Fallback fb) {
     __shared__ WarpRowTile<F> tiles[8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int w = blockIdx.x * 8 + warp;
@@ -133,8 +136,27 @@ __global__ void __launch_bounds__(256, 4) k_warp_rows(Side side, Params p, const
         T.u.G[lane][lane] = (lane < f) ? T.u.G[lane][lane] + reg : 1.f;
     }
     __syncwarp();
-    float* dst = G_aug + (int64_t)w * F * (F + 1);
-    for (int e = lane; e < F * (F + 1); e += 32) dst[e] = T.u.G[e / (F + 1)][e % (F + 1)];
+    if (X_out == nullptr) {
+        float* dst = G_aug + (int64_t)w * F * (F + 1);
+        for (int e = lane; e < F * (F + 1); e += 32) dst[e] = T.u.G[e / (F + 1)][e % (F + 1)];
+        return;
+    }
+    // The system never leaves the SM: the warp solves it here, exactly as
+    // k_solve_rows does from the stored copy.
+    float v[F];
+#pragma unroll
+    for (int j = 0; j < F; ++j) v[j] = (lane < F) ? T.u.G[lane][j] : 0.f;
+    const float rhs = (lane < F) ? T.u.G[lane][F] : 0.f;
+    float x;
+    int flags;
+    float ratio;
+    warp_solve<F>(v, rhs, p.f, p.gram_mode == GRAM_ASYM, p.ratio_max, x, flags, ratio);
+    if (lane < p.f) X_out[i * p.f + lane] = x;
+    if (lane == 0) {
+        if (flags_out) flags_out[i] = flags;
+        record_flags(cnt, flags, ratio);
+        fallback_push(fb, flags, i);
+    }
 }
 
 }  // namespace als

@@ -649,6 +649,10 @@ def warmstart_leg(budget=None, train_seeds=(101, 102, 103, 104, 105), held_seeds
     def med(key, sub):
         vals = [d[key][sub] for d in per_seed if d[key][sub] is not None]
         return float(statistics.median(vals)) if vals else None
+    def med_gain(j, what):
+        vals = [d["gain"]["to_plain_after"][j][what] for d in per_seed]
+        vals = [v for v in vals if v is not None]
+        return float(statistics.median(vals)) if vals else None
     runs = ("plain",) + tuple(f"warm_p{q}" for q in precisions)
     names = {"plain": "FP32 from random M^(0)", "warm_p0": "warm start, FP32",
              "warm_p1": "warm start, TF32 + 1 refinement", "warm_p2": "warm start, BF16 + 2 refinements"}
@@ -660,6 +664,10 @@ def warmstart_leg(budget=None, train_seeds=(101, 102, 103, 104, 105), held_seeds
             "median_sweeps": {k: med("sweeps_to_target", k) for k in runs},
             "median_ms": {k: med("ms_to_target", k) for k in runs},
             "warm_start_chosen": sum(d["chosen"] == "warm" for d in per_seed), "held_out_seeds": len(per_seed),
+            "early_stopping": {str(j): {"to_rmse_plain_has_after_sweeps": j,
+                                        "median_sweeps_saved": med_gain(j, "sweeps_saved"),
+                                        "median_ms_saved": med_gain(j, "ms_saved")}
+                               for j in per_seed[0]["gain"]["to_plain_after"]},
             "runs": {k: names[k] for k in runs}, "per_seed": per_seed}
 
 

@@ -10,7 +10,8 @@ M^(0) is the judge: both starts run `judge_after` sweeps (default 5), and the
 fit continues from the warm start only if its test RMSE there is not worse;
 otherwise it falls back to M^(0). The gain is reported as sweeps and
 milliseconds to the target RMSE saved by the warm start (negative when it
-loses).
+loses), and, for early stopping, as the sweeps and milliseconds the warm run
+saves in reaching the RMSE the plain run has after a given number of sweeps.
 
 This module only orchestrates; features, the networks (forward, backward,
 Adam) and ALS run in libcore_als.so.
@@ -136,6 +137,17 @@ def judge(nets: Pair, problem, n_f, lam, budget, M0, sweeps, target=None, precis
             "ms_saved": (reach_ms["plain"] - reach_ms[first_warm]) if reach["plain"] and reach[first_warm] else None,
             "rmse_at_judge": {"plain": curves["plain"][k - 1], "warm": curves[first_warm][k - 1]},
             "final_rmse": {"plain": curves["plain"][-1], "warm": curves[first_warm][-1]}}
+    # Early-stopping view: sweeps and ms the warm run needs to reach the RMSE
+    # the plain run has after j sweeps (None if it never does), for j = the
+    # judging point and half the sweeps.
+    gain["to_plain_after"] = {}
+    for j in sorted({k, max(1, sweeps // 2)}):
+        goal = curves["plain"][j - 1]
+        rw = next((q + 1 for q, e in enumerate(curves[first_warm]) if e <= goal), None)
+        gain["to_plain_after"][j] = {
+            "rmse": goal, "warm_sweeps": rw,
+            "sweeps_saved": (j - rw) if rw else None,
+            "ms_saved": (times["plain"][j - 1] - times[first_warm][rw - 1]) if rw else None}
     out = {"target": target, "curves": curves, "chosen": chosen, "judge_after": k, "sweeps_to_target": reach,
            "ms_to_target": reach_ms, "warm_start_ms": warm_ms, "gain": gain}
     out["curves"]["warm"] = curves[first_warm]

@@ -104,3 +104,11 @@ def test_warm_start_judged_against_plain_als(core):
         assert g["ms_saved"] == pytest.approx(res["ms_to_target"]["plain"] - res["ms_to_target"]["warm_p0"])
     else:
         assert g["sweeps_saved"] is None and g["ms_saved"] is None
+    for j, e in g["to_plain_after"].items():
+        rw = e["warm_sweeps"]
+        assert e["rmse"] == c["plain"][j - 1]
+        if rw is None:
+            assert min(c["warm"]) > e["rmse"]
+        else:
+            assert c["warm"][rw - 1] <= e["rmse"] and all(x > e["rmse"] for x in c["warm"][:rw - 1])
+            assert e["sweeps_saved"] == j - rw

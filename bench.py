@@ -151,6 +151,58 @@ def oracle_sample(p, M0, lam, r, n_user_rows, n_item_rows, seed):
     return (p.n_u + p.n_m) / t_sweep, done, t_sweep
 
 
+def small_leg(M0_seed=1000, seed=1):
+    """The oracle-sized workload ('small': 1000 x 500, n_f = 10, 5 % of the
+    cells, lambda 0.1, r = 0.5) timed whole: the GPU sweep (CUDA events) and
+    the FP64 oracle's full sweep on all host cores and on one core, from the
+    same M^(0), with the test RMSE of both after the same sweeps."""
+    import torch
+    import oracle
+    from paper_2509_18024_gb300 import core_als
+    w = dict(synth.WORKLOADS["small"])
+    p = synth.make_workload("small", seed=seed)
+    M0 = synth.init_factor(p.n_m, p.f, M0_seed)
+    sweeps = w["sweeps"]
+    eng = core_als.CoreALS(p.f, w["lam"], w["budget"])
+    Ru, Ri = core_als.DeviceCSR.from_host(p.train_rows), core_als.DeviceCSR.from_host(p.train_cols)
+    M = torch.as_tensor(M0).cuda()
+    U = torch.empty((p.n_u, p.f), device="cuda")
+    eng.sweep(Ru, Ri, U, M)  # plans and workspace
+    M.copy_(torch.as_tensor(M0))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(sweeps):
+        eng.sweep(Ru, Ri, U, M)
+    b.record()
+    torch.cuda.synchronize()
+    gpu_ms = a.elapsed_time(b) / sweeps
+    test = tuple(np.asarray(t) for t in (p.test_u, p.test_m, p.test_r))
+    gpu_rmse = oracle.rmse(*test, U.cpu().numpy().astype(np.float64), M.cpu().numpy().astype(np.float64))
+    eng.close()
+    oracle.build()
+    res = {}
+    all_cores = oracle.num_threads()
+    for cores in (all_cores, 1):
+        oracle.set_threads(cores)
+        try:
+            t0 = time.perf_counter()
+            Uo, Mo = oracle.fit(p.train_rows, p.train_cols, M0, w["lam"], w["budget"], sweeps)
+            dt = time.perf_counter() - t0
+        finally:
+            oracle.set_threads(all_cores)
+        res[f"oracle_{'all' if cores == all_cores else 'one'}_cores"] = {
+            "cores": cores, "ms_per_sweep": 1e3 * dt / sweeps,
+            "row_solves_per_s": (p.n_u + p.n_m) * sweeps / dt}
+        oracle_rmse = oracle.rmse(*test, Uo, Mo)
+    return {"workload": f"small: {p.n_u} x {p.n_m}, {p.train_rows.nnz} training cells, n_f={p.f}, "
+                        f"lambda={w['lam']}, r={w['budget']}, {sweeps} sweeps from the same M^(0)",
+            "gpu": {"ms_per_sweep": gpu_ms, "row_solves_per_s": (p.n_u + p.n_m) / (gpu_ms * 1e-3),
+                    "test_rmse": gpu_rmse},
+            **res, "oracle_test_rmse": oracle_rmse,
+            "rmse_rel_diff": abs(gpu_rmse - oracle_rmse) / oracle_rmse}
+
+
 def reference_arm(args, p, w, M0, r):
     import oracle
     oracle.build()
@@ -845,6 +897,18 @@ def main():
                                    "sample": f"{done} random rows (40000 user + 8000 item rows), one half-sweep "
                                              f"each, extrapolated to a full sweep by observed entries "
                                              f"(est. {t_sweep:.1f} s per sweep)"}
+            # The same oracle on one core (a smaller sample of the same rows' kind).
+            all_cores = oracle.num_threads()
+            oracle.set_threads(1)
+            try:
+                rate1, done1, t1 = oracle_sample(p, M0, w["lam"], r, 4000, 800, 7)
+            finally:
+                oracle.set_threads(all_cores)
+            out["cpu_baseline"]["one_core"] = {
+                "value": rate1, "unit": UNIT, "cores": 1,
+                "sample": f"{done1} random rows (4000 user + 800 item rows), extrapolated likewise "
+                          f"(est. {t1:.1f} s per sweep)"}
+            out["small_workload"] = small_leg(M0_seed=1000)
         if world == 1 and not args.no_sim:
             out["simulation_metrics"] = simulation_leg()
         if world == 1 and not args.no_batch:

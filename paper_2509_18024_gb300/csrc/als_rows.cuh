@@ -40,8 +40,9 @@ struct SplitHistCols {
 };
 // Resident CTAs per SM that k_split_gram is compiled for: one for the
 // tensor-core engines (their tiles fill shared memory; without the bound the
-// compiler holds them to 64 registers), two or four on the CUDA cores.
-__host__ __device__ constexpr int split_gram_min_blocks(int F, int eng) { return eng != 0 ? 1 : (F >= 32 ? 2 : 4); }
+// compiler holds them to 64 registers), three (as many as the shared memory
+// allows at F = 32) or four on the CUDA cores.
+__host__ __device__ constexpr int split_gram_min_blocks(int F, int eng) { return eng != 0 ? 1 : (F >= 32 ? 3 : 4); }
 __host__ __device__ constexpr int split_hist_cols(int F) { return F < 32 ? F : 32; }
 
 // Mask words per position.

@@ -837,7 +837,7 @@ __global__ void k_split_init(Side side, Params p, SplitPlan sp, SplitState st) {
 }
 
 template <int F>
-__global__ void __launch_bounds__(kCtaThreads) k_split_hist(Side side, Params p, SplitPlan sp, SplitState st,
+__global__ void __launch_bounds__(kCtaThreads, 6) k_split_hist(Side side, Params p, SplitPlan sp, SplitState st,
                                                             int pass) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     uint32_t (*hist)[kHistRow] = reinterpret_cast<uint32_t (*)[kHistRow]>(smem_raw);

@@ -349,10 +349,10 @@ __global__ void __launch_bounds__(32) k_solve_replay(const float* __restrict__ G
 // (reg_lu_block); the results are the same bit for bit, and the deferred
 // form needs 168 registers, so three CTAs share an SM. One warp
 // back-substitutes from U. Rows never move (partial pivoting through the
-// step order). store != 0: each row's block of L / U
-// entries goes back to G_aug (L before the row's own pivot step, U from it
-// on) and the physical row of each step to perm_buf, the form k_solve_replay
-// reads.
+// step order). The system comes into shared memory with one bulk copy.
+// store != 0: each row's block of L / U entries goes back to G_aug (L before
+// the row's own pivot step, U from it on) and the physical row of each step
+// to perm_buf, the form k_solve_replay reads.
 template <int F>
 struct RegSolve {
     static constexpr int NT = F;      // threads per system
